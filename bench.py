@@ -1,0 +1,406 @@
+#!/usr/bin/env python3
+"""Benchmark: batched inverse dynamics (RNEA) on GB300.
+
+Headline workload: one 32-link serial chain (the seeded random-robot recipe
+of the experiments, Sec. V), B = 65536 joint states per step, FP32 arithmetic;
+one step = one rnea_batch call over the batch (forward scan + backward scan,
+Algorithm 1). Beside it, on the same GPU and run: the same workload in FP64,
+and the host-array entry point (copies in the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun), every rank times its own
+B = 65536 batch on its own GPU (instances are independent: no collective on
+the data path); value = all ranks' evaluations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_LINKS = 32
+BATCH = 65536
+METRIC = "RNEA evals/s at n=32,B=65536 FP32 vs FP64; adjoint evals/s; % of roofline"
+UNIT = "evals/s"
+WORKLOAD = "rnea_n32_B65536"
+ROTATE = 8  # input sets cycled between steps; 8 x 33.5 MB > 2 x L2 (129 MB)
+FLOP_PER_LINK = 280     # FP32/FP64 arithmetic of the joint-frame formulation, FMA = 2
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) stamped on arrival; regions marked by wall time."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.samples = []
+        self.regions = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._reader, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _reader(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid:
+                continue
+            try:
+                sm, smax = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            active = [r for r, v in zip(self.REASONS, parts[5:9]) if v.lower() == "active"]
+            self.samples.append((time.time(), sm, smax, active))
+
+    def region(self, t0, t1):
+        self.regions.append((t0, t1))
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        inside = [s for s in self.samples if any(a - 0.05 <= s[0] <= b + 0.05 for a, b in self.regions)]
+        use = inside if inside else self.samples
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = sorted({r for s in use for r in s[3]})
+        return {"sm_mhz": statistics.median(s[1] for s in use),
+                "sm_max_mhz": max(s[2] for s in use), "reasons": reasons,
+                "samples": len(use), "samples_in_timed_regions": len(inside)}
+
+
+# ---------------------------------------------------------------- profiles
+
+def recorded_traffic(kernel_tag):
+    """Per-launch DRAM bytes from the committed ncu summary for this kernel, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_sources_hash():
+        return None
+    return float(m.group(1))
+
+
+def kernel_sources_hash():
+    d = os.path.join(ROOT, "paper_1609_04493_gb300", "csrc")
+    hs = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            hs.update(f.encode())
+            hs.update(open(os.path.join(d, f), "rb").read())
+    return hs.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except ValueError:
+            return {}
+    return {}
+
+
+# --------------------------------------------------------------- our arm
+
+def make_inputs(torch, dev, dtype, sets, seed0):
+    import chaingen
+
+    out = []
+    for r in range(sets):
+        st = chaingen.make_states(BATCH, N_LINKS, seed=seed0 + r)
+        d = {k: torch.from_numpy(st[k]).to(device=dev, dtype=dtype) for k in ("q", "qd", "qdd")}
+        d["tau"] = torch.empty_like(d["q"])
+        out.append(d)
+    return out
+
+
+def capture(torch, rd, model, sets, count, variant=0):
+    """CUDA graph of `count` rnea_batch launches cycling through the input sets."""
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rd.rnea(model, sets[0]["q"], sets[0]["qd"], sets[0]["qdd"], out=sets[0]["tau"],
+                variant=variant)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            for k in range(count):
+                x = sets[k % len(sets)]
+                rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"], variant=variant)
+    torch.cuda.synchronize()
+    return g
+
+
+def timed_graph(torch, g, dist, sampler):
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier(dist)
+    if sampler is not None:
+        sampler.region(t0, t1)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args):
+    import torch
+
+    import chaingen
+    import paper_1609_04493_gb300 as rd
+
+    rank, world, local = dist_env()
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rd.load()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else None) if rank == 0 else None
+
+    chain = chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED)
+    model = rd.Model(chain)
+    K, W = args.steps, args.warmup
+
+    # ---- FP32 headline
+    sets32 = make_inputs(torch, dev, torch.float32, ROTATE, 1000 + 100 * rank)
+    gw = capture(torch, rd, model, sets32, max(W, 1))
+    gw.replay()
+    torch.cuda.synchronize()
+    g32 = capture(torch, rd, model, sets32, K)
+    t32 = max_over_ranks(dist, timed_graph(torch, g32, dist, sampler))
+    value = world * BATCH * K / t32
+    ms_step = t32 / K * 1e3
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_links": N_LINKS, "batch": BATCH,
+                      "global_batch": BATCH * world, "parallelism": f"replicas{world}",
+                      "l2": f"{ROTATE} rotating input sets "
+                            f"({ROTATE * BATCH * N_LINKS * 16 / 1e6:.0f} MB) > L2",
+                      "seed": chaingen.BASE_SEED},
+           "gpu_launches": K}
+
+    # roofline of the dominant kernel (the FP32 RNEA kernel: one launch per step)
+    avg_launch = t32 / K
+    flops = FLOP_PER_LINK * N_LINKS * BATCH
+    peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    achieved = flops / avg_launch / 1e12
+    traffic = recorded_traffic("rnea_fp32_n32_B65536")
+    res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
+                       "frac": achieved / peak32, "traffic": traffic,
+                       "kernel": "rnea_serial_kernel<float>",
+                       "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                       "hbm": {"achieved_gbs": BATCH * N_LINKS * 16 / avg_launch / 1e9,
+                               "peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)}}
+
+    if not args.quick:
+        # ---- FP64 on the same GPU
+        K64 = max(3, min(K, 200))
+        del g32, gw
+        sets64 = make_inputs(torch, dev, torch.float64, 4, 2000 + 100 * rank)
+        gw64 = capture(torch, rd, model, sets64, 3)
+        gw64.replay()
+        torch.cuda.synchronize()
+        g64 = capture(torch, rd, model, sets64, K64)
+        t64 = max_over_ranks(dist, timed_graph(torch, g64, dist, sampler))
+        fp64_flops = FLOP_PER_LINK * N_LINKS * BATCH / (t64 / K64) / 1e12
+        res["fp64"] = {"value": world * BATCH * K64 / t64, "unit": UNIT, "steps": K64,
+                       "ms_per_step": t64 / K64 * 1e3, "achieved_tflops": fp64_flops,
+                       "peak_tflops_nominal": FP64_NOMINAL_TFLOPS,
+                       "frac": fp64_flops / FP64_NOMINAL_TFLOPS}
+        del g64, gw64, sets64
+
+        # ---- end to end through the host-array entry point
+        st = chaingen.make_states(BATCH, N_LINKS, seed=3000 + rank)
+        host = [torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("q", "qd", "qdd")]
+        out = torch.empty_like(host[0]).pin_memory()
+        for _ in range(3):
+            rd.rnea_host(model, *host, out=out)
+        Ke = max(3, min(K, 50))
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            rd.rnea_host(model, *host, out=out)
+        te = max_over_ranks(dist, time.perf_counter() - t0)
+        barrier(dist)
+        res["e2e"] = {"value": world * BATCH * Ke / te, "unit": UNIT, "steps": Ke,
+                      "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
+                      "d2h_bytes_per_step": BATCH * N_LINKS * 4,
+                      "api": "rnea_batch_host (pinned host arrays, FP32)"}
+
+    if sampler is not None:
+        res["clocks"] = sampler.stop()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(target_s=10.0)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+# -------------------------------------------------------- CPU (oracle) arm
+
+def _cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(target_s=10.0, threads=None):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of the
+    headline workload (same chain, fresh states), batch split over threads."""
+    import chaingen
+    import oracle
+
+    threads = threads or _cpu_threads()
+    chain = chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED)
+    probe = chaingen.make_states(256 * threads, N_LINKS, seed=4242)
+    t0 = time.perf_counter()
+    oracle.rnea_threaded(chain, probe["q"], probe["qd"], probe["qdd"], threads=threads)
+    rate = 256 * threads / max(time.perf_counter() - t0, 1e-6)
+    sample = int(min(max(rate * target_s / threads, 1024), 4 * BATCH))
+    st = chaingen.make_states(sample, N_LINKS, seed=4343)
+    t0 = time.perf_counter()
+    oracle.rnea_threaded(chain, st["q"], st["qd"], st["qdd"], threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sample} states of the n=32 chain (FP64 oracle, {threads} threads, "
+                      f"{dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import chaingen
+    import oracle
+
+    threads = _cpu_threads()
+    chain = chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED)
+    probe = chaingen.make_states(256 * threads, N_LINKS, seed=4242)
+    t0 = time.perf_counter()
+    oracle.rnea_threaded(chain, probe["q"], probe["qd"], probe["qdd"], threads=threads)
+    rate = 256 * threads / max(time.perf_counter() - t0, 1e-6)
+    total_budget = 90.0
+    per_step = int(max(64, min(BATCH, rate * total_budget / (args.steps + args.warmup))))
+    st = chaingen.make_states(per_step, N_LINKS, seed=4343)
+    for _ in range(args.warmup):
+        oracle.rnea_threaded(chain, st["q"], st["qd"], st["qdd"], threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rnea_threaded(chain, st["q"], st["qd"], st["qdd"], threads=threads)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    sample = (f"{per_step} of the {BATCH} states per step, n=32 chain, FP64 oracle on "
+              f"{threads} host threads")
+    res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_links": N_LINKS, "batch": BATCH,
+                      "global_batch": BATCH * world, "parallelism": f"replicas{world}",
+                      "seed": chaingen.BASE_SEED},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

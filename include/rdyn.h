@@ -1,0 +1,141 @@
+/*
+ * rdyn.h -- batched serial-chain dynamics on one GB300 GPU (sm_103a).
+ *
+ * C ABI of librdyn.so. No C++ or PyTorch types cross it: host arrays are
+ * plain double pointers, batch arrays are raw device pointers, and the CUDA
+ * stream is passed as an opaque pointer (a cudaStream_t; NULL = the legacy
+ * default stream).
+ *
+ * Method: "Parallel Dynamics Computation using Prefix Sum Operations"
+ * (Yang, Wu, Pan; arXiv 1609.04493). Inverse dynamics is the recursive
+ * Newton-Euler algorithm (Sec. II-A, Eqs. id-forward and id-backward), cast
+ * as a forward scan over SE(3) x se(3)^2 (Sec. III-B, Eq. scan-id-vel-acc)
+ * and a backward scan of reaction wrenches (Sec. III-C, Eq. id-bkwd-scan).
+ *
+ * Conventions shared by every entry point:
+ *   - twists are (v, w), linear part first; wrenches are (f, n), paired
+ *     with twists as F^T V;
+ *   - f_{i-1,i} = M_i exp([S_i] q_i) maps frame-i coordinates to frame i-1;
+ *     M_i is its value at q_i = 0 and S_i is expressed in frame i;
+ *   - the base frame is frame 0; V_0 and dV_0 are expressed in it; gravity
+ *     enters as a base acceleration (dV_0 = (0, 0, 9.81, 0, 0, 0) for
+ *     gravity along -z);
+ *   - F_{n+1} is the wrench that link n exerts on its environment,
+ *     expressed in frame n.
+ *
+ * Error behaviour: every int-returning call returns RD_OK (0) on success or
+ * a negative RD_ERR_* code; rd_last_error() then gives a message for the
+ * calling thread. Calls that take a stream are asynchronous with respect to
+ * the host: an error detected on the host is returned at once, a launch
+ * failure is returned as RD_ERR_CUDA, and faults inside a kernel surface on
+ * the stream as usual CUDA errors.
+ */
+#ifndef RDYN_H
+#define RDYN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handle to a robot model resident on one device. */
+typedef struct rd_model rd_model;
+
+enum rd_dtype { RD_F32 = 0, RD_F64 = 1 };
+
+enum rd_status {
+    RD_OK = 0,
+    RD_ERR_ARG = -1,     /* null pointer, bad size, invalid model data */
+    RD_ERR_DTYPE = -2,   /* dtype not RD_F32 / RD_F64 */
+    RD_ERR_RANGE = -3,   /* n outside [1, RD_MAX_LINKS] or B negative */
+    RD_ERR_CUDA = -4,    /* a CUDA runtime call failed */
+    RD_ERR_TIMEOUT = -5, /* a bounded device wait ran out */
+    RD_ERR_ALLOC = -6    /* host or device allocation failed (create only) */
+};
+
+/* Kernel variant for rnea_batch. */
+enum rd_variant {
+    RD_VARIANT_AUTO = 0,    /* library's choice for (n, B, dtype) */
+    RD_VARIANT_SERIAL = 1,  /* one thread per instance, per-link state in shared memory */
+    RD_VARIANT_SERIAL_RECOMPUTE = 2 /* one thread per instance, backward sweep re-derives
+                                       V_{i-1}, dV_{i-1} from V_i, dV_i; no per-link state */
+};
+/* Lane-parallel scan: L lanes of one warp per instance, L in {2,4,8,16,32};
+ * each lane owns ceil(n/L) consecutive links, lanes combine their segments
+ * with warp-shuffle log-step semigroup scans (Sec. III). */
+#define RD_VARIANT_SCAN(L) (0x100 | (L))
+
+#define RD_MAX_LINKS 128
+
+/*
+ * rd_model_create -- upload a serial chain of n revolute joints.
+ *
+ *   n        number of links / joints, 1 <= n <= RD_MAX_LINKS.
+ *   M        host, n*12 doubles: per link the rotation of M_i (row-major
+ *            3x3) then its translation (3). (Sec. II-A, Eq. id-forward.)
+ *   S        host, n*6 doubles: joint twist S_i = (v, w) in frame i; |w| = 1
+ *            and w.v = 0 (revolute joint) are required.
+ *   inertia  host, n*10 doubles: (m, c_x, c_y, c_z, I_xx, I_yy, I_zz, I_xy,
+ *            I_xz, I_yz): mass, centre of mass in frame i, and rotational
+ *            inertia about the centre of mass in frame i's axes (m > 0, the
+ *            3x3 inertia positive definite).
+ *   out      receives the handle.
+ *
+ * The arrays are copied; the caller keeps ownership. The model lives on the
+ * current CUDA device, and every batch call must run with that device
+ * current. Allocation happens here, never in the batch calls.
+ * Errors: RD_ERR_RANGE (n), RD_ERR_ARG (null pointer, non-unit axis, pitched
+ * twist, non-positive mass or inertia), RD_ERR_ALLOC, RD_ERR_CUDA.
+ */
+int rd_model_create(int n, const double *M, const double *S, const double *inertia,
+                    rd_model **out);
+
+/* Free a model (NULL is ignored). Must not race with work using it. */
+void rd_model_destroy(rd_model *model);
+
+/* Number of links of a model, or RD_ERR_ARG for NULL. */
+int rd_model_links(const rd_model *model);
+
+/*
+ * rnea_batch -- inverse dynamics for B states of one chain:
+ *     tau = ID(q, qd, qdd, V_0, dV_0, F_{n+1})   (Sec. II-A; Algorithm 1)
+ *
+ *   model    from rd_model_create (n links).
+ *   B        batch size, B >= 0 (B == 0 is a no-op).
+ *   dtype    RD_F32 or RD_F64: element type of q, qd, qdd and tau, and the
+ *            arithmetic precision.
+ *   q, qd, qdd  device, [B, n] row-major, contiguous, dtype elements.
+ *   tau      device, [B, n] row-major output; may not alias the inputs.
+ *   base     host, 18 doubles {V_0[6], dV_0[6], F_{n+1}[6]} shared by the
+ *            batch, or NULL for a base at rest under gravity along -z
+ *            (dV_0 = (0, 0, 9.81, 0, 0, 0), F_{n+1} = 0).
+ *   variant  rd_variant value or RD_VARIANT_SCAN(L).
+ *   stream   cudaStream_t to launch on.
+ *
+ * Errors: RD_ERR_ARG (null model/pointers with B > 0, bad variant),
+ * RD_ERR_DTYPE, RD_ERR_RANGE (B < 0), RD_ERR_CUDA (launch failure).
+ */
+int rnea_batch(const rd_model *model, int B, int dtype, const void *q, const void *qd,
+               const void *qdd, void *tau, const double *base, int variant, void *stream);
+
+/*
+ * rnea_batch_host -- rnea_batch on HOST arrays: copies q, qd, qdd to the
+ * device, runs the kernel, copies tau back, and waits for the result.
+ * Uses device buffers owned by the model, grown on demand (this call may
+ * allocate device memory; rnea_batch never does). For pinned host memory the
+ * copies run at full link speed. Same argument meaning as rnea_batch.
+ */
+int rnea_batch_host(rd_model *model, int B, int dtype, const void *q, const void *qd,
+                    const void *qdd, void *tau, const double *base, int variant,
+                    void *stream);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *rd_last_error(void);
+
+/* Library ABI version (major * 100 + minor). */
+int rd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RDYN_H */

@@ -1,0 +1,24 @@
+"""Batched serial-chain dynamics on one GB300 GPU.
+
+A thin Python binding over the C ABI of ``librdyn.so`` (include/rdyn.h):
+argument marshalling only. Every step of the computation runs in the
+library's CUDA kernels; there is no CPU or PyTorch fallback, and calls fail
+loudly when the library or a CUDA device is missing. PyTorch supplies
+device memory and streams.
+"""
+from .binding import (  # noqa: F401
+    RD_F32,
+    RD_F64,
+    RD_MAX_LINKS,
+    RD_VARIANT_AUTO,
+    RD_VARIANT_SERIAL,
+    RD_VARIANT_SERIAL_RECOMPUTE,
+    RD_VARIANT_SCAN,
+    RdError,
+    Model,
+    load,
+    library_path,
+    rnea,
+    rnea_host,
+    default_base,
+)

@@ -1,0 +1,202 @@
+"""ctypes binding of librdyn.so (include/rdyn.h). Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+RD_F32 = 0
+RD_F64 = 1
+RD_MAX_LINKS = 128
+RD_VARIANT_AUTO = 0
+RD_VARIANT_SERIAL = 1
+RD_VARIANT_SERIAL_RECOMPUTE = 2
+
+
+def RD_VARIANT_SCAN(lanes):
+    return 0x100 | int(lanes)
+
+
+_ERRORS = {-1: "RD_ERR_ARG", -2: "RD_ERR_DTYPE", -3: "RD_ERR_RANGE", -4: "RD_ERR_CUDA",
+           -5: "RD_ERR_TIMEOUT", -6: "RD_ERR_ALLOC"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class RdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path():
+    return _build.SO
+
+
+def load(build_if_missing=True):
+    """Load librdyn.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.SO):
+            raise RuntimeError(f"librdyn.so not found at {_build.SO}; run the build first")
+        lib = ctypes.CDLL(_build.SO)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.POINTER(ctypes.c_double)
+        lib.rd_model_create.argtypes = [I, D, D, D, ctypes.POINTER(P)]
+        lib.rd_model_create.restype = I
+        lib.rd_model_destroy.argtypes = [P]
+        lib.rd_model_destroy.restype = None
+        lib.rd_model_links.argtypes = [P]
+        lib.rd_model_links.restype = I
+        lib.rnea_batch.argtypes = [P, I, I, P, P, P, P, D, I, P]
+        lib.rnea_batch.restype = I
+        lib.rnea_batch_host.argtypes = [P, I, I, P, P, P, P, D, I, P]
+        lib.rnea_batch_host.restype = I
+        lib.rd_last_error.argtypes = []
+        lib.rd_last_error.restype = ctypes.c_char_p
+        lib.rd_version.argtypes = []
+        lib.rd_version.restype = I
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RdError(rc, _lib.rd_last_error().decode(errors="replace"))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_base(gravity=9.81):
+    """{V_0, dV_0, F_{n+1}} for a base at rest under gravity along -z."""
+    b = np.zeros(18)
+    b[8] = gravity
+    return b
+
+
+class Model:
+    """A serial chain resident on the current CUDA device (rd_model_create)."""
+
+    def __init__(self, M, S=None, inertia=None):
+        if S is None and inertia is None:  # a chain object with .M, .S, .inertia
+            M, S, inertia = M.M, M.S, M.inertia
+        lib = load()
+        self._M = np.ascontiguousarray(M, dtype=np.float64).reshape(-1, 12)
+        self._S = np.ascontiguousarray(S, dtype=np.float64).reshape(-1, 6)
+        self._J = np.ascontiguousarray(inertia, dtype=np.float64).reshape(-1, 10)
+        n = self._M.shape[0]
+        if self._S.shape[0] != n or self._J.shape[0] != n:
+            raise ValueError("M, S and inertia must describe the same number of links")
+        h = ctypes.c_void_p()
+        _check(lib.rd_model_create(n, _dptr(self._M), _dptr(self._S), _dptr(self._J),
+                                   ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.rd_model_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _dtype_code(t):
+    import torch
+
+    if t.dtype == torch.float32:
+        return RD_F32
+    if t.dtype == torch.float64:
+        return RD_F64
+    raise TypeError(f"dtype {t.dtype} not supported (float32 or float64)")
+
+
+def _base_arg(base):
+    if base is None:
+        return None, None
+    b = np.ascontiguousarray(base, dtype=np.float64).reshape(18)
+    return b, _dptr(b)
+
+
+def _check_batch(model, *ts):
+    import torch
+
+    ref = ts[0]
+    for t in ts:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("expected torch tensors")
+        if not t.is_cuda:
+            raise ValueError("tensors must be on a CUDA device (use rnea_host for host arrays)")
+        if t.dtype != ref.dtype or t.shape != ref.shape:
+            raise ValueError("all batch tensors must share dtype and shape")
+        if not t.is_contiguous():
+            raise ValueError("batch tensors must be contiguous [B, n]")
+    if ref.dim() != 2 or ref.shape[1] != model.n:
+        raise ValueError(f"expected shape [B, {model.n}], got {tuple(ref.shape)}")
+
+
+def rnea(model, q, qd, qdd, out=None, base=None, variant=RD_VARIANT_AUTO, stream=None):
+    """tau = ID(q, qd, qdd, V_0, dV_0, F_{n+1}) on the GPU (rnea_batch)."""
+    import torch
+
+    _check_batch(model, q, qd, qdd)
+    if out is None:
+        out = torch.empty_like(q)
+    else:
+        _check_batch(model, q, out)
+    if stream is None:
+        stream = torch.cuda.current_stream(q.device)
+    keep, bp = _base_arg(base)
+    _check(_lib.rnea_batch(model.handle, q.shape[0], _dtype_code(q), q.data_ptr(), qd.data_ptr(),
+                           qdd.data_ptr(), out.data_ptr(), bp, int(variant),
+                           ctypes.c_void_p(stream.cuda_stream)))
+    del keep
+    return out
+
+
+def rnea_host(model, q, qd, qdd, out=None, base=None, variant=RD_VARIANT_AUTO, stream=None):
+    """Inverse dynamics on host arrays (rnea_batch_host): the library copies the
+    inputs to the device, runs the kernel and copies tau back before returning.
+    Accepts CPU torch tensors or numpy arrays; pinned tensors copy fastest."""
+    import torch
+
+    arrs = [q, qd, qdd]
+    if isinstance(q, np.ndarray):
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)) for a in arrs]
+    for a in arrs:
+        if a.is_cuda or not a.is_contiguous() or a.shape != arrs[0].shape or a.dtype != arrs[0].dtype:
+            raise ValueError("rnea_host expects contiguous host arrays of one shape and dtype")
+    if arrs[0].dim() != 2 or arrs[0].shape[1] != model.n:
+        raise ValueError(f"expected shape [B, {model.n}]")
+    if out is None:
+        out = torch.empty_like(arrs[0])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    keep, bp = _base_arg(base)
+    load()
+    _check(_lib.rnea_batch_host(model.handle, arrs[0].shape[0], _dtype_code(arrs[0]),
+                                arrs[0].data_ptr(), arrs[1].data_ptr(), arrs[2].data_ptr(),
+                                out.data_ptr(), bp, int(variant),
+                                ctypes.c_void_p(stream.cuda_stream)))
+    del keep
+    return out

@@ -1,0 +1,31 @@
+// rdyn_internal.h -- shared host-side declarations of librdyn.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rdyn.h"
+#include "spatial.cuh"
+
+struct rd_model {
+    int n = 0;
+    int device = 0;
+    float *d_c32 = nullptr;   // n * kLinkConsts, joint-frame constants (FP32)
+    double *d_c64 = nullptr;  // same in FP64
+    double TnR[9];            // joint frame of link n (for F_{n+1})
+    double Tnp[3];
+    std::vector<double> host_c64;
+    // device staging for the host-pointer entry points, grown on demand
+    void *d_io = nullptr;
+    size_t io_bytes = 0;
+    std::mutex io_mu;
+};
+
+extern thread_local std::string g_rd_error;
+int rd_fail(int code, const char *fmt, ...);
+int rd_cuda_fail(cudaError_t e, const char *what);
+void rd_convert_base(const rd_model *m, const double *base, double out[18]);

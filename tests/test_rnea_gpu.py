@@ -1,0 +1,138 @@
+"""GPU parity of rnea_batch against the FP64 oracle, through the C ABI.
+
+Error metric (per instance, maximised over the batch):
+    max_i |tau_i - tau*_i| / max_i |tau*_i|.
+Bars: FP64 GPU <= 1e-10; FP32 GPU <= 1e-4. The oracle always sees exactly the
+values the GPU saw (FP32 inputs widened to FP64), so the measured error is
+arithmetic error only.
+"""
+import numpy as np
+import pytest
+
+import chaingen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"float32": 1e-4, "float64": 1e-10}
+VARIANTS = {"auto": 0, "serial": 1, "recompute": 2}
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def run_case(rd, n, B, dtype, variant, seed=5, base=None, chain=None):
+    torch = _torch()
+    ch = chain or chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    st = chaingen.make_states(B, n, seed=seed)
+    np_dt = np.float32 if dtype == "float32" else np.float64
+    host = {k: st[k].astype(np_dt) for k in ("q", "qd", "qdd")}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    model = rd.Model(ch)
+    tau = rd.rnea(model, dev["q"], dev["qd"], dev["qdd"], base=base, variant=variant)
+    torch.cuda.synchronize()
+    ref = oracle.rnea(ch, *(host[k].astype(np.float64) for k in ("q", "qd", "qdd")), base=base)
+    return tau.cpu().numpy().astype(np.float64), ref
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("variant", ["serial", "recompute"])
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 31, 32, 33, 64, 100, 128])
+def test_rnea_parity(cuda_lib, n, dtype, variant):
+    B = 1000  # several blocks and a ragged tail
+    if variant == "serial" and dtype == "float64" and n > 100:
+        pytest.skip("per-link state of this chain exceeds shared memory; recompute covers it")
+    tau, ref = run_case(cuda_lib, n, B, dtype, VARIANTS[variant])
+    err = oracle.rel_err(tau, ref)
+    assert err <= TOL[dtype], f"n={n} {dtype} {variant}: rel err {err:.3e}"
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_rnea_base_motion_and_external_wrench(cuda_lib, dtype):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25,      # V_0
+                     0.3, 1.1, 9.81, -0.2, 0.4, 0.1,       # dV_0
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])      # F_{n+1}
+    tau, ref = run_case(cuda_lib, 9, 333, dtype, 0, base=base)
+    assert oracle.rel_err(tau, ref) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("B", [0, 1, 31, 63, 65, 257])
+def test_rnea_edge_batches(cuda_lib, B):
+    torch = _torch()
+    n = 5
+    if B == 0:
+        model = cuda_lib.Model(chaingen.make_chain(n))
+        z = torch.empty((0, n), device="cuda")
+        out = cuda_lib.rnea(model, z, z, z)
+        assert out.shape == (0, n)
+        return
+    tau, ref = run_case(cuda_lib, n, B, "float64", 0)
+    assert oracle.rel_err(tau, ref) <= TOL["float64"]
+
+
+def test_rnea_closed_form_pendulum(cuda_lib):
+    torch = _torch()
+    m, l, Ixx = 1.7, 0.45, 0.03
+    ch = chaingen.pendulum(m, l, Ixx)
+    model = cuda_lib.Model(ch)
+    q = torch.linspace(-3, 3, 97, dtype=torch.float64, device="cuda").reshape(-1, 1)
+    qd = torch.full_like(q, 0.7)
+    qdd = torch.cos(q)
+    tau = cuda_lib.rnea(model, q, qd, qdd).cpu().numpy()
+    qh, qddh = q.cpu().numpy(), qdd.cpu().numpy()
+    expect = (m * l * l + Ixx) * qddh + m * 9.81 * l * np.sin(qh)
+    assert np.max(np.abs(tau - expect)) < 1e-12
+
+
+def test_rnea_variants_agree_fp64(cuda_lib):
+    a, _ = run_case(cuda_lib, 24, 500, "float64", 1)
+    b, _ = run_case(cuda_lib, 24, 500, "float64", 2)
+    assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(a))
+
+
+def test_rnea_full_size_fp32_n32(cuda_lib):
+    """n = 32, B = 65536 in FP32 with the launch the benchmark times; the oracle
+    checks every instance (about a second of CPU)."""
+    tau, ref = run_case(cuda_lib, 32, 65536, "float32", 0, seed=1609)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
+@pytest.mark.parametrize("n", [16, 100])
+def test_rnea_full_batch_other_lengths_sampled(cuda_lib, n):
+    """B = 65536 at n = 16 and 100: every 64th instance checked against the oracle."""
+    torch = _torch()
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    st = chaingen.make_states(65536, n, seed=77)
+    host = {k: st[k].astype(np.float32) for k in ("q", "qd", "qdd")}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    model = cuda_lib.Model(ch)
+    tau = cuda_lib.rnea(model, dev["q"], dev["qd"], dev["qdd"]).cpu().numpy()
+    idx = np.arange(0, 65536, 64)
+    ref = oracle.rnea(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd")))
+    assert oracle.rel_err(tau[idx], ref) <= TOL["float32"]
+
+
+def test_rnea_host_entry_point(cuda_lib):
+    torch = _torch()
+    n, B = 12, 700
+    ch = chaingen.make_chain(n)
+    st = chaingen.make_states(B, n, seed=9)
+    model = cuda_lib.Model(ch)
+    args = [torch.from_numpy(st[k]).pin_memory() for k in ("q", "qd", "qdd")]
+    tau = cuda_lib.rnea_host(model, *args).numpy()
+    ref = oracle.rnea(ch, st["q"], st["qd"], st["qdd"])
+    assert oracle.rel_err(tau, ref) <= TOL["float64"]
+
+
+def test_rnea_rejects_wrong_shapes(cuda_lib):
+    torch = _torch()
+    model = cuda_lib.Model(chaingen.make_chain(6))
+    x = torch.zeros((10, 5), device="cuda")
+    with pytest.raises(ValueError):
+        cuda_lib.rnea(model, x, x, x)
+    y = torch.zeros((10, 6), device="cuda", dtype=torch.float16)
+    with pytest.raises(TypeError):
+        cuda_lib.rnea(model, y, y, y)
