@@ -56,13 +56,23 @@ enum rd_status {
 enum rd_variant {
     RD_VARIANT_AUTO = 0,    /* library's choice for (n, B, dtype) */
     RD_VARIANT_SERIAL = 1,  /* one thread per instance, per-link state in shared memory */
-    RD_VARIANT_SERIAL_RECOMPUTE = 2 /* one thread per instance, backward sweep re-derives
-                                       V_{i-1}, dV_{i-1} from V_i, dV_i; no per-link state */
+    RD_VARIANT_SERIAL_RECOMPUTE = 2, /* one thread per instance, backward sweep re-derives
+                                        V_{i-1}, dV_{i-1} from V_i, dV_i; no per-link state */
+    RD_VARIANT_SERIAL_RECOMPUTE_CS = 3 /* as 2, keeping cos/sin of q_i in shared memory */
 };
 /* Lane-parallel scan: L lanes of one warp per instance, L in {2,4,8,16,32};
  * each lane owns ceil(n/L) consecutive links, lanes combine their segments
  * with warp-shuffle log-step semigroup scans (Sec. III). */
 #define RD_VARIANT_SCAN(L) (0x100 | (L))
+/* OR-able flag: in FP32, evaluate sin/cos of q_i by a 2*pi range reduction
+ * plus the hardware approximation (absolute error ~4e-7) instead of the
+ * default accurate library routine. Faster; the torque error can then exceed
+ * 1e-4 of max|tau| on instances whose torques nearly cancel. */
+#define RD_FLAG_FAST_TRIG 0x1000
+/* OR-able tuning field: threads per block of the one-thread-per-instance
+ * kernels (32, 64 or 128; 0 = library default). */
+#define RD_TUNE_BLOCK(threads) ((threads) == 32 ? (5 << 16) : (threads) == 64 ? (6 << 16) \
+                                : (threads) == 128 ? (7 << 16) : 0)
 
 #define RD_MAX_LINKS 128
 
@@ -77,7 +87,7 @@ enum rd_variant {
  *   inertia  host, n*10 doubles: (m, c_x, c_y, c_z, I_xx, I_yy, I_zz, I_xy,
  *            I_xz, I_yz): mass, centre of mass in frame i, and rotational
  *            inertia about the centre of mass in frame i's axes (m > 0, the
- *            3x3 inertia positive definite).
+ *            3x3 inertia positive semi-definite; a point mass is allowed).
  *   out      receives the handle.
  *
  * The arrays are copied; the caller keeps ownership. The model lives on the

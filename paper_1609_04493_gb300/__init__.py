@@ -13,7 +13,10 @@ from .binding import (  # noqa: F401
     RD_VARIANT_AUTO,
     RD_VARIANT_SERIAL,
     RD_VARIANT_SERIAL_RECOMPUTE,
+    RD_VARIANT_SERIAL_RECOMPUTE_CS,
+    RD_TUNE_BLOCK,
     RD_VARIANT_SCAN,
+    RD_FLAG_FAST_TRIG,
     RdError,
     Model,
     load,

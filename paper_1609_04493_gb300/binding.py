@@ -15,10 +15,18 @@ RD_MAX_LINKS = 128
 RD_VARIANT_AUTO = 0
 RD_VARIANT_SERIAL = 1
 RD_VARIANT_SERIAL_RECOMPUTE = 2
+RD_VARIANT_SERIAL_RECOMPUTE_CS = 3
+
+
+RD_FLAG_FAST_TRIG = 0x1000
 
 
 def RD_VARIANT_SCAN(lanes):
     return 0x100 | int(lanes)
+
+
+def RD_TUNE_BLOCK(threads):
+    return {32: 5 << 16, 64: 6 << 16, 128: 7 << 16}.get(int(threads), 0)
 
 
 _ERRORS = {-1: "RD_ERR_ARG", -2: "RD_ERR_DTYPE", -3: "RD_ERR_RANGE", -4: "RD_ERR_CUDA",

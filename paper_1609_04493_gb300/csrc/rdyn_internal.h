@@ -29,3 +29,9 @@ extern thread_local std::string g_rd_error;
 int rd_fail(int code, const char *fmt, ...);
 int rd_cuda_fail(cudaError_t e, const char *what);
 void rd_convert_base(const rd_model *m, const double *base, double out[18]);
+int rd_rnea_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
+                         const void *qdd, void *tau, const double *base18, int variant,
+                         cudaStream_t s);
+int rd_rnea_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd,
+                         const void *qdd, void *tau, const double *base18, int variant,
+                         cudaStream_t s);

@@ -109,17 +109,21 @@ int joint_frame(int link, const double *S, Rigid &T)
     return RD_OK;
 }
 
-bool spd3(const double I[3][3])
+// Symmetric positive semi-definite test by principal minors (a point mass,
+// I_c = 0, is allowed), with a tolerance relative to the trace.
+bool psd3(const double I[3][3])
 {
-    double a = I[0][0];
-    if (!(a > 0)) return false;
-    double l10 = I[1][0] / std::sqrt(a);
-    double b = I[1][1] - l10 * l10;
-    if (!(b > 0)) return false;
-    double l20 = I[2][0] / std::sqrt(a);
-    double l21 = (I[2][1] - l20 * l10) / std::sqrt(b);
-    double c = I[2][2] - l20 * l20 - l21 * l21;
-    return c > 0;
+    double tr = std::fabs(I[0][0]) + std::fabs(I[1][1]) + std::fabs(I[2][2]);
+    double eps = 1e-12 * (tr + 1e-300);
+    for (int i = 0; i < 3; ++i)
+        if (!(I[i][i] >= -eps)) return false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (!(I[i][i] * I[j][j] - I[i][j] * I[j][i] >= -eps * tr)) return false;
+    double det = I[0][0] * (I[1][1] * I[2][2] - I[1][2] * I[2][1]) -
+                 I[0][1] * (I[1][0] * I[2][2] - I[1][2] * I[2][0]) +
+                 I[0][2] * (I[1][0] * I[2][1] - I[1][1] * I[2][0]);
+    return det >= -eps * tr * tr;
 }
 
 }  // namespace
@@ -159,9 +163,9 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
         if (!(m > 0) || !std::isfinite(m))
             return rd_fail(RD_ERR_ARG, "link %d: mass %g must be positive", i, m);
         double Ic[3][3] = {{in[4], in[7], in[8]}, {in[7], in[5], in[9]}, {in[8], in[9], in[6]}};
-        if (!spd3(Ic))
+        if (!psd3(Ic))
             return rd_fail(RD_ERR_ARG, "link %d: inertia about the centre of mass is not "
-                                       "positive definite", i);
+                                       "positive semi-definite", i);
         Rigid Mi;
         for (int k = 0; k < 9; ++k) Mi.R[k] = M[12 * i + k];
         for (int k = 0; k < 3; ++k) Mi.p[k] = M[12 * i + 9 + k];

@@ -1,0 +1,164 @@
+// rnea_launch.cuh -- variant choice and launches of the one-thread-per-
+// instance RNEA kernels; included once per element type (rnea_f32.cu,
+// rnea_f64.cu) so the two instantiation sets compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "rdyn_internal.h"
+#include "rnea_serial.cuh"
+
+namespace rdyn {
+namespace {
+
+template <typename T>
+BaseParams<T> make_base(const double b[18])
+{
+    BaseParams<T> p;
+    for (int k = 0; k < 6; ++k) {
+        p.V0[k] = (T)b[k];
+        p.dV0[k] = (T)b[6 + k];
+        p.Fn[k] = (T)b[12 + k];
+    }
+    return p;
+}
+
+int max_smem_optin(int device)
+{
+    static std::atomic<int> cache[64];
+    if (device < 0 || device >= 64) return 48 * 1024;
+    int v = cache[device].load();
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+            cudaSuccess)
+            v = 48 * 1024;
+        cache[device].store(v);
+    }
+    return v;
+}
+
+// Raise a kernel's dynamic shared-memory limit once per device.
+template <typename K>
+cudaError_t allow_smem(K kern, int device, std::atomic<uint64_t> &done)
+{
+    uint64_t bit = 1ull << (device & 63);
+    if (done.load() & bit) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_smem_optin(device));
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
+
+template <typename T>
+size_t serial_smem(int n, int block, int mode, bool vec)
+{
+    size_t s = (size_t)n * kLinkConsts * sizeof(T);
+    if (vec) s += (size_t)stage_bytes_per_thread<T>() * block;
+    s += (size_t)n * state_bytes_per_link<T>(mode) * block;
+    return s;
+}
+
+template <typename T, int BLOCK, int MODE, bool VEC, bool FAST>
+int launch_serial_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                    void *tau, const double *base18, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    const int n = m->n;
+    size_t smem = serial_smem<T>(n, BLOCK, MODE, VEC);
+    auto kern = rnea_serial_kernel<T, BLOCK, MODE, VEC, FAST>;
+    cudaError_t e = allow_smem(kern, m->device, configured);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+    const T *consts = nullptr;
+    if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
+    else consts = reinterpret_cast<const T *>(m->d_c64);
+    unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    kern<<<grid, BLOCK, smem, stream>>>(consts, n, B, static_cast<const T *>(q),
+                                        static_cast<const T *>(qd), static_cast<const T *>(qdd),
+                                        static_cast<T *>(tau), make_base<T>(base18));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea kernel launch");
+    return RD_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Vector loads (and the cp.async ring) when rows are whole 16-byte chunks and
+// the ring still fits; element loads otherwise.
+template <typename T, int BLOCK, int MODE>
+int launch_serial(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                  void *tau, const double *base18, bool fast, cudaStream_t stream)
+{
+    const size_t limit = (size_t)max_smem_optin(m->device);
+    bool vec = (m->n % 4 == 0) && aligned16(q) && aligned16(qd) && aligned16(qdd) &&
+               aligned16(tau) && serial_smem<T>(m->n, BLOCK, MODE, true) <= limit;
+    if (!vec && serial_smem<T>(m->n, BLOCK, MODE, false) > limit)
+        return rd_fail(RD_ERR_ARG, "rnea_batch: %zu bytes of shared memory needed, %zu available",
+                       serial_smem<T>(m->n, BLOCK, MODE, false), limit);
+    if constexpr (sizeof(T) == 4) {
+        if (fast)
+            return vec ? launch_serial_k<T, BLOCK, MODE, true, true>(m, B, q, qd, qdd, tau, base18, stream)
+                       : launch_serial_k<T, BLOCK, MODE, false, true>(m, B, q, qd, qdd, tau, base18, stream);
+    }
+    return vec ? launch_serial_k<T, BLOCK, MODE, true, false>(m, B, q, qd, qdd, tau, base18, stream)
+               : launch_serial_k<T, BLOCK, MODE, false, false>(m, B, q, qd, qdd, tau, base18, stream);
+}
+
+template <typename T, int MODE>
+int launch_mode(const rd_model *m, int block, int B, const void *q, const void *qd,
+                const void *qdd, void *tau, const double *base18, bool fast, cudaStream_t s)
+{
+    switch (block) {
+    case 32: return launch_serial<T, 32, MODE>(m, B, q, qd, qdd, tau, base18, fast, s);
+    case 64: return launch_serial<T, 64, MODE>(m, B, q, qd, qdd, tau, base18, fast, s);
+    case 128: return launch_serial<T, 128, MODE>(m, B, q, qd, qdd, tau, base18, fast, s);
+    default: return rd_fail(RD_ERR_ARG, "rnea_batch: block size %d not built (32, 64, 128)", block);
+    }
+}
+
+template <typename T>
+int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd, void *tau,
+             const double *base18, int variant, cudaStream_t s)
+{
+    const int n = m->n;
+    const size_t limit = (size_t)max_smem_optin(m->device);
+    const bool fast = (variant & RD_FLAG_FAST_TRIG) != 0;
+    int block = (variant >> 16) & 0xff;
+    if (block) block = 1 << block;
+    variant &= 0xfff;
+    if (variant == RD_VARIANT_AUTO) {
+        // Sweep on GB300 at B = 65536 (modes x block sizes): per-link state in
+        // shared memory wins while it is small (FP32 n <= 32, FP64 n <= 16);
+        // FP64 up to n = 32 keeps only cos/sin; longer chains re-derive the
+        // motion in the backward sweep.
+        if (n <= (sizeof(T) == 4 ? 32 : 16) && serial_smem<T>(n, 32, kStore, true) <= limit / 4) {
+            variant = RD_VARIANT_SERIAL;
+            if (!block) block = n > 16 ? 32 : 64;
+        } else if (sizeof(T) == 8 && n <= 32) {
+            variant = RD_VARIANT_SERIAL_RECOMPUTE_CS;
+            if (!block) block = 32;
+        } else {
+            variant = RD_VARIANT_SERIAL_RECOMPUTE;
+            if (!block) block = sizeof(T) == 4 ? 64 : 32;
+        }
+    }
+    if (variant == RD_VARIANT_SERIAL) {
+        if (!block) {
+            block = serial_smem<T>(n, 64, kStore, false) <= limit / 2 ? 64 : 32;
+            if (serial_smem<T>(n, 32, kStore, false) > limit)
+                return rd_fail(RD_ERR_ARG, "rnea_batch: per-link state of %d links does not fit in "
+                                           "shared memory; use RD_VARIANT_SERIAL_RECOMPUTE", n);
+        }
+        return launch_mode<T, kStore>(m, block, B, q, qd, qdd, tau, base18, fast, s);
+    }
+    if (!block) block = 64;
+    if (variant == RD_VARIANT_SERIAL_RECOMPUTE)
+        return launch_mode<T, kRecompute>(m, block, B, q, qd, qdd, tau, base18, fast, s);
+    if (variant == RD_VARIANT_SERIAL_RECOMPUTE_CS)
+        return launch_mode<T, kRecomputeCS>(m, block, B, q, qd, qdd, tau, base18, fast, s);
+    return rd_fail(RD_ERR_ARG, "rnea_batch: unknown variant 0x%x", variant);
+}
+
+}  // namespace
+}  // namespace rdyn

@@ -83,7 +83,7 @@ def test_model_create_rejects_bad_input_on_host(lib):
     J[3, 4:7] = [1.0, 1.0, 1.0]
     J[3, 7] = 5.0  # Ixy too large: not positive definite
     rc, msg, _, _ = _create(lib, 4, ch.M, ch.S, J)
-    assert rc == -1 and "positive definite" in msg
+    assert rc == -1 and "positive semi-definite" in msg
 
 
 def test_batch_calls_reject_bad_arguments_on_host(lib):

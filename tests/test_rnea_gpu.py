@@ -87,6 +87,33 @@ def test_rnea_closed_form_pendulum(cuda_lib):
     assert np.max(np.abs(tau - expect)) < 1e-12
 
 
+@pytest.mark.parametrize("n", [8, 32, 100])
+@pytest.mark.parametrize("variant", [1, 2])
+def test_rnea_fast_trig_flag(cuda_lib, n, variant):
+    """RD_FLAG_FAST_TRIG (SFU sine/cosine after a 2*pi reduction) on chains with
+    several links stays within the FP32 bar."""
+    tau, ref = run_case(cuda_lib, n, 1000, "float32", variant | cuda_lib.RD_FLAG_FAST_TRIG)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
+def test_rnea_unaligned_rows_fall_back_to_element_loads(cuda_lib):
+    """Rows that are not 16-byte aligned (a tensor view offset by one element)."""
+    torch = _torch()
+    n, B = 8, 300
+    ch = chaingen.make_chain(n)
+    st = chaingen.make_states(B, n, seed=3)
+    model = cuda_lib.Model(ch)
+    bufs = []
+    for k in ("q", "qd", "qdd"):
+        flat = torch.zeros(B * n + 1, dtype=torch.float32, device="cuda")
+        flat[1:] = torch.from_numpy(st[k].astype(np.float32).ravel()).cuda()
+        bufs.append(flat[1:].view(B, n))
+    out_flat = torch.zeros(B * n + 1, dtype=torch.float32, device="cuda")
+    tau = cuda_lib.rnea(model, *bufs, out=out_flat[1:].view(B, n)).cpu().numpy()
+    ref = oracle.rnea(ch, *(st[k].astype(np.float32).astype(np.float64) for k in ("q", "qd", "qdd")))
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
 def test_rnea_variants_agree_fp64(cuda_lib):
     a, _ = run_case(cuda_lib, 24, 500, "float64", 1)
     b, _ = run_case(cuda_lib, 24, 500, "float64", 2)
