@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "rdyn_internal.h"
+#include "rnea_scan.cuh"
 #include "rnea_serial.cuh"
 
 namespace rdyn {
@@ -117,6 +118,56 @@ int launch_mode(const rd_model *m, int block, int B, const void *q, const void *
     }
 }
 
+template <typename T, int L, int K, bool FAST>
+int launch_scan_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                  void *tau, const double *base18, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    const int n = m->n;
+    const size_t smem = (size_t)n * kLinkConsts * sizeof(T);
+    auto kern = rnea_scan_kernel<T, L, K, FAST>;
+    cudaError_t e = allow_smem(kern, m->device, configured);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+    const T *consts = nullptr;
+    if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
+    else consts = reinterpret_cast<const T *>(m->d_c64);
+    const long long threads = (long long)B * L;
+    const unsigned grid = (unsigned)((threads + 127) / 128);
+    kern<<<grid, 128, smem, stream>>>(consts, n, B, static_cast<const T *>(q),
+                                      static_cast<const T *>(qd), static_cast<const T *>(qdd),
+                                      static_cast<T *>(tau), make_base<T>(base18));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea scan kernel launch");
+    return RD_OK;
+}
+
+template <typename T, int L, bool FAST>
+int launch_scan_l(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                  void *tau, const double *base18, cudaStream_t s)
+{
+    const int k = (m->n + L - 1) / L;
+    if (k <= 1) return launch_scan_k<T, L, 1, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    if (k <= 2) return launch_scan_k<T, L, 2, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    if (k <= 4) return launch_scan_k<T, L, 4, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    if (k <= 8) return launch_scan_k<T, L, 8, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    return rd_fail(RD_ERR_ARG, "rnea_batch: %d lanes cannot hold %d links (at most 8 per lane)",
+                   L, m->n);
+}
+
+template <typename T, bool FAST>
+int launch_scan(const rd_model *m, int lanes, int B, const void *q, const void *qd,
+                const void *qdd, void *tau, const double *base18, cudaStream_t s)
+{
+    switch (lanes) {
+    case 2: return launch_scan_l<T, 2, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    case 4: return launch_scan_l<T, 4, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    case 8: return launch_scan_l<T, 8, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    case 16: return launch_scan_l<T, 16, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    case 32: return launch_scan_l<T, 32, FAST>(m, B, q, qd, qdd, tau, base18, s);
+    default: return rd_fail(RD_ERR_ARG, "rnea_batch: scan lanes %d not in {2,4,8,16,32}", lanes);
+    }
+}
+
 template <typename T>
 int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd, void *tau,
              const double *base18, int variant, cudaStream_t s)
@@ -127,6 +178,20 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     int block = (variant >> 16) & 0xff;
     if (block) block = 1 << block;
     variant &= 0xfff;
+    if (variant == RD_VARIANT_AUTO && B <= 152 * 32 && n <= 128) {
+        // Fewer instances than one warp per SM: the serial recursion leaves the
+        // GPU idle, and splitting each chain over lanes (the scans of Sec. III)
+        // cuts latency. Measured: n = 7, B = 1024 FP64 30 us with 8 lanes vs 43
+        // serial; n = 32, B = 1024 FP32 5.1 us with 16 lanes vs 8.4 serial;
+        // from B = 8192 on the serial form wins.
+        int lanes = 2;
+        while (lanes < 16 && lanes < n) lanes <<= 1;
+        while (lanes * 8 < n) lanes <<= 1;
+        if constexpr (sizeof(T) == 4) {
+            if (fast) return launch_scan<T, true>(m, lanes, B, q, qd, qdd, tau, base18, s);
+        }
+        return launch_scan<T, false>(m, lanes, B, q, qd, qdd, tau, base18, s);
+    }
     if (variant == RD_VARIANT_AUTO) {
         // Sweep on GB300 at B = 65536 (modes x block sizes): per-link state in
         // shared memory wins while it is small (FP32 n <= 32, FP64 n <= 16);
@@ -157,6 +222,13 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         return launch_mode<T, kRecompute>(m, block, B, q, qd, qdd, tau, base18, fast, s);
     if (variant == RD_VARIANT_SERIAL_RECOMPUTE_CS)
         return launch_mode<T, kRecomputeCS>(m, block, B, q, qd, qdd, tau, base18, fast, s);
+    if ((variant & 0xf00) == 0x100) {
+        const int lanes = variant & 0xff;
+        if constexpr (sizeof(T) == 4) {
+            if (fast) return launch_scan<T, true>(m, lanes, B, q, qd, qdd, tau, base18, s);
+        }
+        return launch_scan<T, false>(m, lanes, B, q, qd, qdd, tau, base18, s);
+    }
     return rd_fail(RD_ERR_ARG, "rnea_batch: unknown variant 0x%x", variant);
 }
 

@@ -163,3 +163,41 @@ def test_rnea_rejects_wrong_shapes(cuda_lib):
     y = torch.zeros((10, 6), device="cuda", dtype=torch.float16)
     with pytest.raises(TypeError):
         cuda_lib.rnea(model, y, y, y)
+
+
+# ---------------------------------------------- lane-parallel scan variant
+
+SCAN_CASES = [(L, n) for L in (2, 4, 8, 16, 32) for n in (1, 2, 5, 7, 16, 31, 32, 33, 64, 100, 128)
+              if n <= 8 * L]
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("L,n", SCAN_CASES)
+def test_rnea_scan_parity(cuda_lib, L, n, dtype):
+    B = 77  # ragged: instances do not fill the last warp
+    tau, ref = run_case(cuda_lib, n, B, dtype, cuda_lib.RD_VARIANT_SCAN(L), seed=11)
+    assert oracle.rel_err(tau, ref) <= TOL[dtype], f"L={L} n={n} {dtype}"
+
+
+@pytest.mark.parametrize("L", [4, 32])
+def test_rnea_scan_equals_serial_fp64(cuda_lib, L):
+    """The scan reaches the serial recursion's result (Sec. III): FP64 to 1e-12."""
+    a, _ = run_case(cuda_lib, 20, 300, "float64", 1, seed=13)
+    b, _ = run_case(cuda_lib, 20, 300, "float64", cuda_lib.RD_VARIANT_SCAN(L), seed=13)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_rnea_scan_base_and_wrench(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    for L in (2, 8, 32):
+        tau, ref = run_case(cuda_lib, 13, 100, "float64", cuda_lib.RD_VARIANT_SCAN(L), base=base)
+        assert oracle.rel_err(tau, ref) <= TOL["float64"], L
+
+
+def test_rnea_scan_rejects_too_many_links(cuda_lib):
+    torch = _torch()
+    model = cuda_lib.Model(chaingen.make_chain(20))
+    x = torch.zeros((4, 20), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea(model, x, x, x, variant=cuda_lib.RD_VARIANT_SCAN(2))
