@@ -51,6 +51,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
+    p.add_argument("--kernel-only", choices=["f32", "f64"], default=None,
+                   help="profiling case: W + K plain launches of the headline kernel, no JSON")
     return p.parse_args()
 
 
@@ -272,12 +274,21 @@ def run_ours(args):
     peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
     achieved = flops / avg_launch / 1e12
     traffic = recorded_traffic("rnea_fp32_n32_B65536")
+    try:
+        fma32 = rd.measure_fma_peak("float32")
+        fma64 = rd.measure_fma_peak("float64")
+    except Exception:  # diagnostic only
+        fma32 = fma64 = None
     res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                        "frac": achieved / peak32, "traffic": traffic,
-                       "kernel": "rnea_serial_kernel<float>",
-                       "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                       "hbm": {"achieved_gbs": BATCH * N_LINKS * 16 / avg_launch / 1e9,
-                               "peak_gbs": measured_peaks().get("hbm_gbs", 6800.0)}}
+                       "kernel": "rnea_serial_kernel<float, 32 threads, shared-memory state>",
+                       "flop_per_link": FLOP_PER_LINK,
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                       "measured_fma_tflops": {"fp32": fma32, "fp64": fma64},
+                       "hbm": {"algorithmic_bytes_per_launch": BATCH * N_LINKS * 16,
+                               "achieved_gbs": BATCH * N_LINKS * 16 / avg_launch / 1e9,
+                               "peak_gbs": measured_peaks().get("hbm_gbs", 6800.0),
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
 
     if not args.quick:
         # ---- FP64 on the same GPU
@@ -293,7 +304,9 @@ def run_ours(args):
         res["fp64"] = {"value": world * BATCH * K64 / t64, "unit": UNIT, "steps": K64,
                        "ms_per_step": t64 / K64 * 1e3, "achieved_tflops": fp64_flops,
                        "peak_tflops_nominal": FP64_NOMINAL_TFLOPS,
-                       "frac": fp64_flops / FP64_NOMINAL_TFLOPS}
+                       "frac_of_nominal": fp64_flops / FP64_NOMINAL_TFLOPS,
+                       "frac_of_measured_fma": (fp64_flops / fma64) if fma64 else None,
+                       "fp32_over_fp64": value / (world * BATCH * K64 / t64)}
         del g64, gw64, sets64
 
         # ---- end to end through the host-array entry point
@@ -394,9 +407,29 @@ def run_reference(args):
     print(json.dumps(res), flush=True)
 
 
+def run_kernel_only(args):
+    """Small profiling case for ncu: the headline launch, W + K times, no graph."""
+    import torch
+
+    import chaingen
+    import paper_1609_04493_gb300 as rd
+
+    rd.load()
+    dt = torch.float32 if args.kernel_only == "f32" else torch.float64
+    model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
+    x = make_inputs(torch, torch.device("cuda", 0), dt, 1, 1000)[0]
+    for _ in range(args.warmup + args.steps):
+        rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"])
+    torch.cuda.synchronize()
+    print(f"kernel-only {args.kernel_only}: {args.warmup + args.steps} launches, "
+          f"max|tau| = {float(x['tau'].abs().max()):.4g}")
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.kernel_only:
+        run_kernel_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

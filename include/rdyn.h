@@ -138,6 +138,14 @@ int rnea_batch_host(rd_model *model, int B, int dtype, const void *q, const void
                     const void *qdd, void *tau, const double *base, int variant,
                     void *stream);
 
+/*
+ * rd_measure_fma_peak -- diagnostic, outside the paper's method: measured
+ * fused-multiply-add throughput of the current device in TFLOP/s (FMA = 2
+ * flops) for RD_F32 or RD_F64, from independent FMA chains on every SM.
+ * Allocates a small device buffer and synchronizes the stream.
+ */
+int rd_measure_fma_peak(int dtype, double *tflops, void *stream);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *rd_last_error(void);
 

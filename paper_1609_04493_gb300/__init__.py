@@ -24,4 +24,5 @@ from .binding import (  # noqa: F401
     rnea,
     rnea_host,
     default_base,
+    measure_fma_peak,
 )

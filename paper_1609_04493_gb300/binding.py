@@ -74,6 +74,8 @@ def load(build_if_missing=True):
         lib.rd_last_error.restype = ctypes.c_char_p
         lib.rd_version.argtypes = []
         lib.rd_version.restype = I
+        lib.rd_measure_fma_peak.argtypes = [I, D, P]
+        lib.rd_measure_fma_peak.restype = I
         _lib = lib
         return lib
 
@@ -85,6 +87,18 @@ def _check(rc):
 
 def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def measure_fma_peak(dtype="float32", stream=None):
+    """Measured FMA throughput of the current GPU in TFLOP/s (diagnostic)."""
+    import torch
+
+    lib = load()
+    out = ctypes.c_double()
+    st = stream or torch.cuda.current_stream()
+    _check(lib.rd_measure_fma_peak(RD_F32 if dtype == "float32" else RD_F64, ctypes.byref(out),
+                                   ctypes.c_void_p(st.cuda_stream)))
+    return out.value
 
 
 def default_base(gravity=9.81):
