@@ -33,6 +33,8 @@
 #ifndef RDYN_H
 #define RDYN_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -137,6 +139,41 @@ int rnea_batch(const rd_model *model, int B, int dtype, const void *q, const voi
 int rnea_batch_host(rd_model *model, int B, int dtype, const void *q, const void *qd,
                     const void *qdd, void *tau, const double *base, int variant,
                     void *stream);
+
+/* Modes of rnea_vjp (OR-able with RD_FLAG_FAST_TRIG). */
+enum rd_vjp_mode {
+    RD_VJP_AUTO = 0,      /* library's choice (FP64 with a large enough workspace: store) */
+    RD_VJP_STORE = 1,     /* keep the forward sweep's state in the workspace */
+    RD_VJP_RECOMPUTE = 2  /* keep nothing: re-derive it by inverting the forward step */
+};
+
+/*
+ * rnea_vjp -- vector-Jacobian product of inverse dynamics for B states:
+ *     gq = d(w^T tau)/dq,  gqd = d(w^T tau)/dqd,  gqdd = d(w^T tau)/dqdd,
+ * with tau = ID(q, qd, qdd, V_0, dV_0, F_{n+1}) (Sec. II-A). The adjoint of the
+ * backward scan runs base -> tip beside the forward scan, and the adjoint of
+ * the forward scan runs tip -> base beside the backward scan. The paper lists
+ * gradient scans as future work (Sec. VI).
+ *
+ *   q, qd, qdd, w     device, [B, n] row-major, dtype elements (w = d loss / d tau).
+ *   gq, gqd, gqdd     device, [B, n] outputs; distinct, not aliasing the inputs.
+ *   base              as in rnea_batch (NULL = rest under gravity along -z).
+ *   mode              rd_vjp_mode value, optionally | RD_FLAG_FAST_TRIG.
+ *   workspace         device scratch for RD_VJP_STORE (16-byte aligned), at least
+ *                     rnea_vjp_workspace_size() bytes; caller-owned; may be NULL
+ *                     for RD_VJP_RECOMPUTE. Its contents are overwritten.
+ *   stream            cudaStream_t.
+ * Errors: RD_ERR_ARG (null/aliased pointers, workspace too small or unaligned,
+ * unknown mode), RD_ERR_DTYPE, RD_ERR_RANGE, RD_ERR_CUDA. Never allocates.
+ */
+int rnea_vjp(const rd_model *model, int B, int dtype, const void *q, const void *qd,
+             const void *qdd, const void *w, void *gq, void *gqd, void *gqdd,
+             const double *base, int mode, void *workspace, size_t workspace_bytes,
+             void *stream);
+
+/* Bytes of workspace rnea_vjp needs in RD_VJP_STORE mode for B states
+ * (n * 20 scalars per state). */
+int rnea_vjp_workspace_size(const rd_model *model, int B, int dtype, size_t *bytes);
 
 /*
  * rd_measure_fma_peak -- diagnostic, outside the paper's method: measured

@@ -23,6 +23,12 @@ from .binding import (  # noqa: F401
     library_path,
     rnea,
     rnea_host,
+    rnea_vjp,
+    rnea_autograd,
+    vjp_workspace_bytes,
+    RD_VJP_AUTO,
+    RD_VJP_STORE,
+    RD_VJP_RECOMPUTE,
     default_base,
     measure_fma_peak,
 )

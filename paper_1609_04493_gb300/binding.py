@@ -19,6 +19,9 @@ RD_VARIANT_SERIAL_RECOMPUTE_CS = 3
 
 
 RD_FLAG_FAST_TRIG = 0x1000
+RD_VJP_AUTO = 0
+RD_VJP_STORE = 1
+RD_VJP_RECOMPUTE = 2
 
 
 def RD_VARIANT_SCAN(lanes):
@@ -74,6 +77,10 @@ def load(build_if_missing=True):
         lib.rd_last_error.restype = ctypes.c_char_p
         lib.rd_version.argtypes = []
         lib.rd_version.restype = I
+        lib.rnea_vjp.argtypes = [P, I, I, P, P, P, P, P, P, P, D, I, P, ctypes.c_size_t, P]
+        lib.rnea_vjp.restype = I
+        lib.rnea_vjp_workspace_size.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_size_t)]
+        lib.rnea_vjp_workspace_size.restype = I
         lib.rd_measure_fma_peak.argtypes = [I, D, P]
         lib.rd_measure_fma_peak.restype = I
         _lib = lib
@@ -222,3 +229,77 @@ def rnea_host(model, q, qd, qdd, out=None, base=None, variant=RD_VARIANT_AUTO, s
                                 ctypes.c_void_p(stream.cuda_stream)))
     del keep
     return out
+
+
+def vjp_workspace_bytes(model, B, dtype_code):
+    """Workspace bytes rnea_vjp needs in store mode for B states."""
+    lib = load()
+    out = ctypes.c_size_t()
+    _check(lib.rnea_vjp_workspace_size(model.handle, int(B), int(dtype_code), ctypes.byref(out)))
+    return out.value
+
+
+def rnea_vjp(model, q, qd, qdd, w, base=None, mode=RD_VJP_AUTO, workspace=None, stream=None,
+             out=None):
+    """(gq, gqd, gqdd) = d(w^T tau)/d(q, qd, qdd) on the GPU (rnea_vjp).
+
+    In store mode (or AUTO with a workspace) the caller may pass a preallocated
+    uint8 CUDA tensor as ``workspace``; for RD_VJP_STORE without one, a tensor of
+    the required size is allocated here (torch's allocator), never in the library."""
+    import torch
+
+    _check_batch(model, q, qd, qdd, w)
+    gq, gqd, gqdd = out if out is not None else (torch.empty_like(q) for _ in range(3))
+    code = _dtype_code(q)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is None and (mode & 0xff) == RD_VJP_STORE:
+        workspace = torch.empty(vjp_workspace_bytes(model, q.shape[0], code), dtype=torch.uint8,
+                                device=q.device)
+    if workspace is not None:
+        ws_ptr, ws_bytes = workspace.data_ptr(), workspace.numel() * workspace.element_size()
+    if stream is None:
+        stream = torch.cuda.current_stream(q.device)
+    keep, bp = _base_arg(base)
+    _check(_lib.rnea_vjp(model.handle, q.shape[0], code, q.data_ptr(), qd.data_ptr(),
+                         qdd.data_ptr(), w.data_ptr(), gq.data_ptr(), gqd.data_ptr(),
+                         gqdd.data_ptr(), bp, int(mode), ws_ptr, ws_bytes,
+                         ctypes.c_void_p(stream.cuda_stream)))
+    del keep
+    return gq, gqd, gqdd
+
+
+def _make_function():
+    import torch
+
+    class RNEAFunction(torch.autograd.Function):
+        """tau = ID(q, qd, qdd) with a backward pass through the adjoint kernel."""
+
+        @staticmethod
+        def forward(ctx, model, q, qd, qdd, base=None, vjp_mode=RD_VJP_RECOMPUTE):
+            q, qd, qdd = q.contiguous(), qd.contiguous(), qdd.contiguous()
+            ctx.model = model
+            ctx.base = base
+            ctx.vjp_mode = vjp_mode
+            ctx.save_for_backward(q, qd, qdd)
+            return rnea(model, q, qd, qdd, base=base)
+
+        @staticmethod
+        def backward(ctx, grad_tau):
+            q, qd, qdd = ctx.saved_tensors
+            gq, gqd, gqdd = rnea_vjp(ctx.model, q, qd, qdd, grad_tau.contiguous(), base=ctx.base,
+                                     mode=ctx.vjp_mode)
+            return None, gq, gqd, gqdd, None, None
+
+    return RNEAFunction
+
+
+_RNEAFunction = None
+
+
+def rnea_autograd(model, q, qd, qdd, base=None, vjp_mode=RD_VJP_RECOMPUTE):
+    """Differentiable inverse dynamics: a torch.autograd.Function whose backward
+    is the library's adjoint kernel."""
+    global _RNEAFunction
+    if _RNEAFunction is None:
+        _RNEAFunction = _make_function()
+    return _RNEAFunction.apply(model, q, qd, qdd, base, vjp_mode)

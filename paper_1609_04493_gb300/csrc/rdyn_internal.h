@@ -35,3 +35,9 @@ int rd_rnea_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd
 int rd_rnea_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd,
                          const void *qdd, void *tau, const double *base18, int variant,
                          cudaStream_t s);
+int rd_vjp_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                        const void *w, void *gq, void *gqd, void *gqdd, const double *base18,
+                        int mode, void *ws, size_t ws_bytes, cudaStream_t s);
+int rd_vjp_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                        const void *w, void *gq, void *gqd, void *gqdd, const double *base18,
+                        int mode, void *ws, size_t ws_bytes, cudaStream_t s);

@@ -1,0 +1,138 @@
+"""GPU parity of rnea_vjp (the adjoint of the two scans) against the oracle's
+complex-step gradient and FP64 central differences, through the C ABI.
+
+Metric: per instance, the largest error over all three gradients divided by
+the largest reference component over all three (relative to max|g|); a single
+gradient can vanish identically (d tau / d qd of one revolute joint).
+Bars: FP64 1e-9, FP32 1e-3.
+"""
+import numpy as np
+import pytest
+
+import chaingen
+import oracle
+
+pytestmark = pytest.mark.gpu
+TOL = {"float32": 1e-3, "float64": 1e-9}
+
+
+def grad_err(g, ref):
+    """max over (gq, gqd, gqdd) and links of |g - g*| / max over the same of |g*|, per
+    instance, maximised over the batch."""
+    a = np.concatenate([np.asarray(x, dtype=np.float64) for x in g], axis=1)
+    r = np.concatenate([np.asarray(x, dtype=np.float64) for x in ref], axis=1)
+    return oracle.rel_err(a, r)
+
+
+def run(rd, n, B, dtype, mode, seed=3, base=None, chain=None):
+    import torch
+
+    ch = chain or chaingen.make_chain(n, seed=chaingen.BASE_SEED + 3 * n)
+    st = chaingen.make_states(B, n, seed=seed, kinds=("q", "qd", "qdd", "w"))
+    npdt = np.float32 if dtype == "float32" else np.float64
+    host = {k: st[k].astype(npdt) for k in st}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    model = rd.Model(ch)
+    g = rd.rnea_vjp(model, dev["q"], dev["qd"], dev["qdd"], dev["w"], base=base, mode=mode)
+    torch.cuda.synchronize()
+    ref = oracle.rnea_grad(ch, *(host[k].astype(np.float64) for k in ("q", "qd", "qdd", "w")),
+                           base=base)
+    return [x.cpu().double().numpy() for x in g], ref, ch, host
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 33])
+def test_vjp_matches_complex_step(cuda_lib, n, dtype, mode):
+    g, ref, _, _ = run(cuda_lib, n, 150, dtype, mode)
+    err = grad_err(g, ref)
+    assert err <= TOL[dtype], f"n={n} {dtype} mode={mode}: {err:.3e}"
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_vjp_n32_fp32_and_fp64(cuda_lib, mode):
+    for dt in ("float32", "float64"):
+        g, ref, _, _ = run(cuda_lib, 32, 64, dt, mode, seed=8)
+        assert grad_err(g, ref) <= TOL[dt]
+
+
+def test_vjp_against_central_differences_fp64(cuda_lib):
+    n, B, h = 6, 20, 1e-6
+    g, _, ch, host = run(cuda_lib, n, B, "float64", 2, seed=21)
+    fds = []
+    for kidx, k in enumerate(("q", "qd", "qdd")):
+        fd = np.empty((B, n))
+        for j in range(n):
+            p = {x: host[x].copy() for x in ("q", "qd", "qdd")}
+            m = {x: host[x].copy() for x in ("q", "qd", "qdd")}
+            p[k][:, j] += h
+            m[k][:, j] -= h
+            tp = oracle.rnea(ch, p["q"], p["qd"], p["qdd"])
+            tm = oracle.rnea(ch, m["q"], m["qd"], m["qdd"])
+            fd[:, j] = np.sum(host["w"] * (tp - tm), axis=1) / (2 * h)
+        fds.append(fd)
+    assert grad_err(g, fds) <= 1e-7
+
+
+def test_vjp_qdd_gradient_is_mass_matrix_times_w(cuda_lib):
+    g, _, ch, host = run(cuda_lib, 12, 40, "float64", 1, seed=5)
+    Mq = oracle.mass_matrix(ch, host["q"])
+    ref = np.einsum("bij,bj->bi", Mq, host["w"])
+    assert oracle.rel_err(g[2], ref) <= 1e-10
+
+
+def test_vjp_base_motion_and_wrench(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    for mode in (1, 2):
+        g, ref, _, _ = run(cuda_lib, 9, 50, "float64", mode, base=base)
+        assert grad_err(g, ref) <= TOL["float64"]
+
+
+def test_vjp_store_equals_recompute(cuda_lib):
+    a, _, _, _ = run(cuda_lib, 40, 300, "float64", 1, seed=4)
+    b, _, _, _ = run(cuda_lib, 40, 300, "float64", 2, seed=4)
+    for x, y in zip(a, b):
+        assert np.max(np.abs(x - y)) <= 1e-10 * np.max(np.abs(x))
+
+
+def test_vjp_store_rejects_small_workspace(cuda_lib):
+    import torch
+
+    model = cuda_lib.Model(chaingen.make_chain(5))
+    x = torch.zeros((8, 5), device="cuda")
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(model, x, x, x, x, mode=cuda_lib.RD_VJP_STORE, workspace=ws)
+
+
+def test_autograd_function_matches_vjp(cuda_lib):
+    import torch
+
+    n, B = 10, 64
+    ch = chaingen.make_chain(n)
+    st = chaingen.make_states(B, n, seed=2, kinds=("q", "qd", "qdd", "w"))
+    model = cuda_lib.Model(ch)
+    q, qd, qdd = (torch.from_numpy(st[k]).cuda().requires_grad_(True) for k in ("q", "qd", "qdd"))
+    w = torch.from_numpy(st["w"]).cuda()
+    tau = cuda_lib.rnea_autograd(model, q, qd, qdd)
+    (tau * w).sum().backward()
+    ref = oracle.rnea_grad(ch, st["q"], st["qd"], st["qdd"], st["w"])
+    assert grad_err([t.cpu().numpy() for t in (q.grad, qd.grad, qdd.grad)], ref) <= 1e-9
+
+
+def test_vjp_full_size_sampled(cuda_lib):
+    """n = 32, B = 8192 FP32 (the adjoint workload), every 64th instance checked."""
+    import torch
+
+    n, B = 32, 8192
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=99, kinds=("q", "qd", "qdd", "w"))
+    host = {k: st[k].astype(np.float32) for k in st}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    model = cuda_lib.Model(ch)
+    for mode in (1, 2):
+        g = cuda_lib.rnea_vjp(model, dev["q"], dev["qd"], dev["qdd"], dev["w"], mode=mode)
+        idx = np.arange(0, B, 64)
+        ref = oracle.rnea_grad(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd", "w")))
+        assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
