@@ -54,6 +54,14 @@ enum rd_status {
     RD_ERR_ALLOC = -6    /* host or device allocation failed (create only) */
 };
 
+/* aba_batch flag: run the z_hat / lambda recursions in the data precision
+ * (FP32 for RD_F32) instead of the default FP64; the articulated-inertia update
+ * and the Omega solves stay in FP64 either way. */
+#define RD_ABA_SCANS_IN_DTYPE 0x1
+
+/* Per-instance status word of aba_batch (0 = fine). */
+#define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */
+
 /* Kernel variant for rnea_batch. */
 enum rd_variant {
     RD_VARIANT_AUTO = 0,    /* library's choice for (n, B, dtype) */
@@ -174,6 +182,31 @@ int rnea_vjp(const rd_model *model, int B, int dtype, const void *q, const void 
 /* Bytes of workspace rnea_vjp needs in RD_VJP_STORE mode for B states
  * (n * 20 scalars per state). */
 int rnea_vjp_workspace_size(const rd_model *model, int B, int dtype, size_t *bytes);
+
+/*
+ * aba_batch -- forward dynamics for B states of one chain:
+ *     qdd = FD(q, qd, tau, V_0, dV_0, F_{n+1})   (Sec. II-B, Eq. fd)
+ * by the articulated-body algorithm: tau_bias = ID(q, qd, 0, ...) (Eq. tau-bias),
+ * the articulated-body inertias (Eq. abi), and the backward / forward linear
+ * recursions of Eq. recursive-fd (the scans of Sec. III-D; Algorithm 3 without
+ * its CPU stage). Arithmetic in dtype, except the articulated-inertia update
+ * and the divisions by Omega_i = S_i^T J_hat_i S_i, which run in FP64.
+ *
+ *   q, qd, tau  device, [B, n] row-major inputs; qdd device [B, n] output.
+ *   base        as in rnea_batch.
+ *   status      device int[B] or NULL: RD_WARN_SINGULAR when an Omega_i <= 0 or a
+ *               non-finite qdd appeared for that instance, else 0.
+ *   workspace   device scratch of at least aba_workspace_size() bytes, 16-byte
+ *               aligned, caller-owned; contents overwritten.
+ * Errors: RD_ERR_ARG (null/aliased pointers, small or unaligned workspace),
+ * RD_ERR_DTYPE, RD_ERR_RANGE, RD_ERR_CUDA. Never allocates.
+ */
+int aba_batch(const rd_model *model, int B, int dtype, const void *q, const void *qd,
+              const void *tau, void *qdd, const double *base, int *status, int flags,
+              void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bytes of workspace aba_batch needs for B states with these flags. */
+int aba_workspace_size(const rd_model *model, int B, int dtype, int flags, size_t *bytes);
 
 /*
  * rd_measure_fma_peak -- diagnostic, outside the paper's method: measured

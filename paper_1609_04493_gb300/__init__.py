@@ -24,6 +24,9 @@ from .binding import (  # noqa: F401
     rnea,
     rnea_host,
     rnea_vjp,
+    aba,
+    aba_workspace_bytes,
+    RD_ABA_SCANS_IN_DTYPE,
     rnea_autograd,
     vjp_workspace_bytes,
     RD_VJP_AUTO,

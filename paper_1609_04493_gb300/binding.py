@@ -81,6 +81,10 @@ def load(build_if_missing=True):
         lib.rnea_vjp.restype = I
         lib.rnea_vjp_workspace_size.argtypes = [P, I, I, ctypes.POINTER(ctypes.c_size_t)]
         lib.rnea_vjp_workspace_size.restype = I
+        lib.aba_batch.argtypes = [P, I, I, P, P, P, P, D, P, I, P, ctypes.c_size_t, P]
+        lib.aba_batch.restype = I
+        lib.aba_workspace_size.argtypes = [P, I, I, I, ctypes.POINTER(ctypes.c_size_t)]
+        lib.aba_workspace_size.restype = I
         lib.rd_measure_fma_peak.argtypes = [I, D, P]
         lib.rd_measure_fma_peak.restype = I
         _lib = lib
@@ -303,3 +307,45 @@ def rnea_autograd(model, q, qd, qdd, base=None, vjp_mode=RD_VJP_RECOMPUTE):
     if _RNEAFunction is None:
         _RNEAFunction = _make_function()
     return _RNEAFunction.apply(model, q, qd, qdd, base, vjp_mode)
+
+
+RD_ABA_SCANS_IN_DTYPE = 0x1
+
+
+def aba_workspace_bytes(model, B, dtype_code, flags=0):
+    """Workspace bytes aba_batch needs for B states."""
+    lib = load()
+    out = ctypes.c_size_t()
+    _check(lib.aba_workspace_size(model.handle, int(B), int(dtype_code), int(flags),
+                                  ctypes.byref(out)))
+    return out.value
+
+
+def aba(model, q, qd, tau, base=None, workspace=None, status=None, out=None, stream=None,
+        flags=0):
+    """qdd = FD(q, qd, tau) on the GPU (aba_batch). A workspace (uint8 CUDA tensor)
+    of aba_workspace_bytes() is taken from torch's allocator when not given; pass a
+    preallocated one (and ``out``) for allocation-free repeated calls. ``status``:
+    optional int32 CUDA tensor [B] receiving per-instance warnings."""
+    import torch
+
+    _check_batch(model, q, qd, tau)
+    qdd = out if out is not None else torch.empty_like(q)
+    code = _dtype_code(q)
+    if workspace is None:
+        workspace = torch.empty(aba_workspace_bytes(model, q.shape[0], code, flags),
+                                dtype=torch.uint8, device=q.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(q.device)
+    keep, bp = _base_arg(base)
+    st_ptr = None
+    if status is not None:
+        if status.dtype != torch.int32 or not status.is_cuda or status.numel() < q.shape[0]:
+            raise ValueError("status must be an int32 CUDA tensor with B entries")
+        st_ptr = status.data_ptr()
+    _check(_lib.aba_batch(model.handle, q.shape[0], code, q.data_ptr(), qd.data_ptr(),
+                          tau.data_ptr(), qdd.data_ptr(), bp, st_ptr, int(flags), workspace.data_ptr(),
+                          workspace.numel() * workspace.element_size(),
+                          ctypes.c_void_p(stream.cuda_stream)))
+    del keep
+    return qdd

@@ -1,0 +1,86 @@
+// aba_launch.cuh -- launches of the forward-dynamics kernel; included once
+// per element type (aba_f32.cu, aba_f64.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "aba.cuh"
+#include "rdyn_internal.h"
+
+namespace rdyn {
+namespace {
+
+inline bool aba_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename T>
+size_t aba_ws_bytes(int n, int B, bool fp32_scans)
+{
+    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
+    const size_t a16 = (a + 255) & ~(size_t)255;
+    return a16 + (size_t)n * kAbaSolveScalars * (size_t)B * (fp32_scans ? sizeof(T) : sizeof(double));
+}
+
+template <typename T, typename Z, int BLOCK, bool VEC>
+int launch_aba_k(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                 void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    const int n = m->n;
+    const size_t smem = (((size_t)n * kLinkConsts * sizeof(T) + 15) & ~(size_t)15) +
+                        (size_t)n * kLinkConsts * sizeof(double);
+    auto kern = aba_kernel<T, Z, BLOCK, VEC>;
+    const uint64_t bit = 1ull << (m->device & 63);
+    if (!(configured.load() & bit)) {
+        int lim = 48 * 1024;
+        cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, m->device);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+        configured.fetch_or(bit);
+    }
+    const T *consts = nullptr;
+    if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
+    else consts = reinterpret_cast<const T *>(m->d_c64);
+    BaseParams<T> bp;
+    for (int k = 0; k < 6; ++k) {
+        bp.V0[k] = (T)base18[k];
+        bp.dV0[k] = (T)base18[6 + k];
+        bp.Fn[k] = (T)base18[12 + k];
+    }
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
+    Z *wsz = reinterpret_cast<Z *>(static_cast<char *>(ws) + ((a + 255) & ~(size_t)255));
+    kern<<<grid, BLOCK, smem, stream>>>(consts, m->d_c64, n, B, static_cast<const T *>(q),
+                                        static_cast<const T *>(qd), static_cast<const T *>(tau),
+                                        static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz,
+                                        bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "aba kernel launch");
+    return RD_OK;
+}
+
+template <typename T>
+int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                 void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
+                 int flags, cudaStream_t s)
+{
+    const bool fp32_scans = sizeof(T) == 4 && (flags & RD_ABA_SCANS_IN_DTYPE);
+    const size_t need = aba_ws_bytes<T>(m->n, B, fp32_scans);
+    if (!ws || ws_bytes < need)
+        return rd_fail(RD_ERR_ARG, "aba_batch: needs a %zu-byte workspace (%zu given)", need,
+                       ws_bytes);
+    if (!aba_aligned16(ws)) return rd_fail(RD_ERR_ARG, "aba_batch: workspace not 16-byte aligned");
+    const bool vec = m->n % 4 == 0 && aba_aligned16(q) && aba_aligned16(qd) &&
+                     aba_aligned16(tau) && aba_aligned16(qdd);
+    if constexpr (sizeof(T) == 4) {
+        if (fp32_scans)
+            return vec ? launch_aba_k<T, T, 64, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+                       : launch_aba_k<T, T, 64, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    }
+    return vec ? launch_aba_k<T, double, 64, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+               : launch_aba_k<T, double, 64, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+}
+
+}  // namespace
+}  // namespace rdyn

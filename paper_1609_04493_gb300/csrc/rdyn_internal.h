@@ -41,3 +41,11 @@ int rd_vjp_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
 int rd_vjp_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                         const void *w, void *gq, void *gqd, void *gqdd, const double *base18,
                         int mode, void *ws, size_t ws_bytes, cudaStream_t s);
+int rd_aba_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                        void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
+                        int flags, cudaStream_t s);
+int rd_aba_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                        void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
+                        int flags, cudaStream_t s);
+size_t rd_aba_ws_bytes_f32(int n, int B, int flags);
+size_t rd_aba_ws_bytes_f64(int n, int B, int flags);

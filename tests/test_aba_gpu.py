@@ -1,0 +1,138 @@
+"""GPU parity of aba_batch (forward dynamics, articulated-body algorithm)
+against the FP64 oracle's ABA and JSIIA, through the C ABI; round trip
+ID(FD(tau)) = tau.
+
+Metric: per instance max_i |qdd - qdd*| / max_i |qdd*|, max over the batch.
+Bars: FP32 (scans in FP32, inertia update and Omega solves in FP64) 1e-3;
+FP64 1e-8 (FD amplifies rounding by the conditioning of M(q)).
+"""
+import numpy as np
+import pytest
+
+import chaingen
+import oracle
+
+pytestmark = pytest.mark.gpu
+TOL = {"float32": 1e-3, "float64": 1e-8}
+
+
+def run(rd, n, B, dtype, seed=31, base=None, chain=None, status=None, flags=0):
+    import torch
+
+    ch = chain or chaingen.make_chain(n, seed=chaingen.BASE_SEED + 5 * n)
+    st = chaingen.make_states(B, n, seed=seed, kinds=("q", "qd", "tau"))
+    npdt = np.float32 if dtype == "float32" else np.float64
+    host = {k: st[k].astype(npdt) for k in st}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    model = rd.Model(ch)
+    qdd = rd.aba(model, dev["q"], dev["qd"], dev["tau"], base=base, status=status, flags=flags)
+    torch.cuda.synchronize()
+    h64 = {k: v.astype(np.float64) for k, v in host.items()}
+    return qdd.cpu().double().numpy(), ch, h64, model
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 33, 64, 100])
+def test_aba_matches_oracle(cuda_lib, n, dtype):
+    qdd, ch, h, _ = run(cuda_lib, n, 300, dtype)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    assert oracle.rel_err(qdd, ref) <= TOL[dtype], f"n={n} {dtype}"
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_aba_matches_jsiia_and_round_trip(cuda_lib, dtype):
+    qdd, ch, h, _ = run(cuda_lib, 24, 120, dtype, seed=3)
+    ref, status = oracle.fd_jsiia(ch, h["q"], h["qd"], h["tau"])
+    assert np.all(status == 0)
+    assert oracle.rel_err(qdd, ref) <= TOL[dtype]
+    back = oracle.rnea(ch, h["q"], h["qd"], qdd)
+    assert oracle.rel_err(back, h["tau"]) <= (1e-3 if dtype == "float32" else 1e-9)
+
+
+def test_aba_gpu_round_trip_through_rnea_fp64(cuda_lib):
+    """FD on the GPU, then ID on the GPU, recovers tau."""
+    import torch
+
+    qdd, ch, h, model = run(cuda_lib, 40, 200, "float64", seed=17)
+    dev = [torch.from_numpy(h[k]).cuda() for k in ("q", "qd")]
+    tau = cuda_lib.rnea(model, dev[0], dev[1], torch.from_numpy(qdd).cuda())
+    assert oracle.rel_err(tau.cpu().numpy(), h["tau"]) <= 1e-9
+
+
+def test_aba_base_motion_and_wrench(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    qdd, ch, h, _ = run(cuda_lib, 11, 90, "float64", base=base)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=base)
+    assert oracle.rel_err(qdd, ref) <= TOL["float64"]
+
+
+def test_aba_single_link_closed_form(cuda_lib):
+    import torch
+
+    m, l, Ixx = 1.7, 0.45, 0.03
+    model = cuda_lib.Model(chaingen.pendulum(m, l, Ixx))
+    q = torch.tensor([[0.4], [-1.1], [2.5]], dtype=torch.float64, device="cuda")
+    qd = torch.tensor([[0.3], [2.0], [-1.0]], dtype=torch.float64, device="cuda")
+    tau = torch.tensor([[1.0], [-3.0], [0.5]], dtype=torch.float64, device="cuda")
+    qdd = cuda_lib.aba(model, q, qd, tau).cpu().numpy()
+    qh, th = q.cpu().numpy(), tau.cpu().numpy()
+    assert np.allclose(qdd, (th - m * 9.81 * l * np.sin(qh)) / (m * l * l + Ixx), atol=1e-13)
+
+
+def test_aba_flags_a_singular_joint(cuda_lib):
+    """A point mass on the joint axis gives Omega = 0: the status word reports it."""
+    import torch
+
+    ch = chaingen.pendulum(1.0, 0.0, 0.0)  # centre of mass on the axis, no inertia
+    model = cuda_lib.Model(ch)
+    x = torch.zeros((5, 1), dtype=torch.float64, device="cuda")
+    status = torch.full((5,), -7, dtype=torch.int32, device="cuda")
+    cuda_lib.aba(model, x, x, x + 1.0, status=status)
+    assert torch.all(status == 1)  # RD_WARN_SINGULAR
+    ch2 = chaingen.make_chain(4)
+    st2 = torch.full((5,), -7, dtype=torch.int32, device="cuda")
+    y = torch.zeros((5, 4), dtype=torch.float64, device="cuda")
+    cuda_lib.aba(cuda_lib.Model(ch2), y, y, y, status=st2)
+    assert torch.all(st2 == 0)
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_aba_full_batch_sampled(cuda_lib, n):
+    """B = 16384 in FP32 (the forward-dynamics workload): every 32nd instance
+    checked against the oracle; round trip on the same sample.
+
+    Round-trip scale: the bias inverse dynamics runs in FP32, and with n = 64
+    links under gravity the bias torques near the base are about 1e3 times the
+    applied tau ~ N(0, 10); its rounding is relative to those torques. So the
+    residual is measured per instance against max(max|tau|, max|tau_bias|),
+    the magnitude of the terms that cancel in tau_hat = tau - tau_bias."""
+    qdd, ch, h, _ = run(cuda_lib, n, 16384, "float32", seed=1609)
+    idx = np.arange(0, 16384, 32)
+    ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
+    assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
+    back = oracle.rnea(ch, h["q"][idx], h["qd"][idx], qdd[idx])
+    bias = oracle.rnea(ch, h["q"][idx], h["qd"][idx], np.zeros_like(qdd[idx]))
+    scale = np.maximum(np.max(np.abs(h["tau"][idx]), axis=1), np.max(np.abs(bias), axis=1))
+    err = np.max(np.abs(back - h["tau"][idx]), axis=1) / scale
+    assert err.max() <= 1e-4 * max(1, n / 16), err.max()
+
+
+def test_aba_rejects_small_workspace(cuda_lib):
+    import torch
+
+    model = cuda_lib.Model(chaingen.make_chain(5))
+    x = torch.zeros((8, 5), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.aba(model, x, x, x, workspace=torch.empty(8, dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("n", [7, 16, 64])
+def test_aba_fp32_scans_flag(cuda_lib, n):
+    """RD_ABA_SCANS_IN_DTYPE: z_hat / lambda in FP32 (inertia update and Omega
+    solves still FP64) meets the FP32 bar on qdd."""
+    B = 16384 if n == 64 else 300
+    qdd, ch, h, _ = run(cuda_lib, n, B, "float32", seed=1609, flags=cuda_lib.RD_ABA_SCANS_IN_DTYPE)
+    idx = np.arange(0, B, max(1, B // 512))
+    ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
+    assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
