@@ -183,6 +183,37 @@ int rnea_vjp(const rd_model *model, int B, int dtype, const void *q, const void 
  * (n * 20 scalars per state). */
 int rnea_vjp_workspace_size(const rd_model *model, int B, int dtype, size_t *bytes);
 
+/* Size of the fixed scratch array behind rnea_vjp_noalloc: 32 MiB per device. */
+#define RD_VJP_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * rnea_vjp_noalloc -- rnea_vjp in RD_VJP_STORE mode for callers that cannot
+ * allocate device memory when they call (a real-time loop with a
+ * no-allocation rule, a plug-in whose host framework owns the memory pool).
+ * This is an interface convenience of the library; the paper has no
+ * counterpart.
+ *
+ * The caller passes inputs and outputs exactly as for rnea_vjp. The store-mode
+ * scratch comes from a file-scope device array of RD_VJP_NOALLOC_SCRATCH_BYTES
+ * that every device loading the library keeps until the process exits; this
+ * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library
+ * routine).
+ *   - Limit: n * 20 * B * sizeof(dtype) must not exceed the scratch size, else
+ *     RD_ERR_RANGE with a message giving both sizes (e.g. n = 32 in FP32 allows
+ *     B <= 13107).
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Sharing: all calls share the one array and it keeps the last call's
+ *     contents; every slot is written before it is read, so nothing is cleared.
+ *     Calls that overlap on the GPU (other streams, other threads) race on it:
+ *     serialise them.
+ * Other errors as for rnea_vjp.
+ */
+int rnea_vjp_noalloc(const rd_model *model, int B, int dtype, const void *q, const void *qd,
+                     const void *qdd, const void *w, void *gq, void *gqd, void *gqdd,
+                     const double *base, void *stream);
+
 /*
  * aba_batch -- forward dynamics for B states of one chain:
  *     qdd = FD(q, qd, tau, V_0, dV_0, F_{n+1})   (Sec. II-B, Eq. fd)
