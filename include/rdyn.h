@@ -239,6 +239,71 @@ int aba_batch(const rd_model *model, int B, int dtype, const void *q, const void
 /* Bytes of workspace aba_batch needs for B states with these flags. */
 int aba_workspace_size(const rd_model *model, int B, int dtype, int flags, size_t *bytes);
 
+/* ---------------------------------------------------------------------------
+ * Fleets: many chains of different lengths, mixed requests in one call.
+ * ------------------------------------------------------------------------- */
+typedef struct rd_fleet rd_fleet;
+typedef struct rd_plan rd_plan;
+
+enum rd_request_kind { RD_REQ_ID = 0, RD_REQ_FD = 1 };
+enum rd_schedule {
+    RD_SCHED_PERSISTENT = 0, /* one launch; resident CTAs pull sorted requests, 32 per warp,
+                                from an atomic counter the call resets first */
+    RD_SCHED_PER_GROUP = 1   /* one launch per run of equal (kind, n), spread over 8
+                                side streams forked from and joined into the call's stream */
+};
+/* Tuning word for RD_SCHED_PERSISTENT: threads per CTA = 2^t, CTAs per SM = c
+ * (0 = library default: 128 threads, 4 CTAs per SM). */
+#define RD_FLEET_TUNE(log2_threads, ctas_per_sm) (((log2_threads) << 8) | (ctas_per_sm))
+
+/*
+ * rd_fleet_create -- upload nrobots chains (Sec. II-A model per robot).
+ *   n        host int[nrobots], 1 <= n[r] <= RD_MAX_LINKS.
+ *   M, S, inertia  host, the robots' arrays (as for rd_model_create) concatenated
+ *            in robot order: sum(n) * 12, * 6 and * 10 doubles.
+ * Allocates device memory; errors as for rd_model_create (message names the robot).
+ */
+int rd_fleet_create(int nrobots, const int *n, const double *M, const double *S,
+                    const double *inertia, rd_fleet **out);
+void rd_fleet_destroy(rd_fleet *fleet);
+
+/*
+ * rd_plan_create -- a fixed set of R requests on a fleet, for data type dtype.
+ *   robot    host int[R]: robot of each request.
+ *   kind     host int[R]: RD_REQ_ID (tau from q, qd, qdd) or RD_REQ_FD (qdd from
+ *            q, qd, tau; articulated-body algorithm with FP64 inertia updates and
+ *            solves, as aba_batch).
+ * Joint data of a call is ragged: request r uses elements [off_r, off_r + n_r)
+ * of every array, off_r the running sum of n over earlier requests
+ * (rd_plan_offsets). The plan sorts requests (forward dynamics first, then by
+ * decreasing n) and allocates its device index arrays, work counter and
+ * forward-dynamics workspace here; fleet_batch allocates nothing.
+ */
+int rd_plan_create(const rd_fleet *fleet, int R, const int *robot, const int *kind, int dtype,
+                   rd_plan **out);
+void rd_plan_destroy(rd_plan *plan);
+/* Length of each ragged data array (sum of n over the requests), -1 for NULL. */
+long long rd_plan_total_joints(const rd_plan *plan);
+/* Host copy of the R request offsets. */
+int rd_plan_offsets(const rd_plan *plan, long long *off);
+/* Number of (kind, n) groups, i.e. launches of RD_SCHED_PER_GROUP. */
+int rd_plan_groups(const rd_plan *plan);
+
+/*
+ * fleet_batch -- evaluate every request of a plan.
+ *   q, qd    device, ragged inputs (plan dtype).
+ *   in2      device: qdd for RD_REQ_ID requests, tau for RD_REQ_FD requests.
+ *   out      device: tau for RD_REQ_ID, qdd for RD_REQ_FD; must not alias inputs.
+ *   base     host {V_0, dV_0, F_{n+1}} for every request (F_{n+1} in each robot's
+ *            frame n), or NULL for rest under gravity along -z.
+ *   status   device int[R] or NULL: RD_WARN_SINGULAR for a forward-dynamics
+ *            request that met Omega_i <= 0 or a non-finite qdd.
+ *   schedule rd_schedule; tune: RD_FLEET_TUNE(...) or 0.
+ * Concurrent calls on one plan race on its counter and workspace.
+ */
+int fleet_batch(const rd_plan *plan, const void *q, const void *qd, const void *in2, void *out,
+                const double *base, int *status, int schedule, int tune, void *stream);
+
 /*
  * rd_measure_fma_peak -- diagnostic, outside the paper's method: measured
  * fused-multiply-add throughput of the current device in TFLOP/s (FMA = 2

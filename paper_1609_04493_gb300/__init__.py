@@ -34,4 +34,12 @@ from .binding import (  # noqa: F401
     RD_VJP_RECOMPUTE,
     default_base,
     measure_fma_peak,
+    Fleet,
+    Plan,
+    fleet_batch,
+    RD_REQ_ID,
+    RD_REQ_FD,
+    RD_SCHED_PERSISTENT,
+    RD_SCHED_PER_GROUP,
+    RD_FLEET_TUNE,
 )

@@ -85,6 +85,24 @@ def load(build_if_missing=True):
         lib.aba_batch.restype = I
         lib.aba_workspace_size.argtypes = [P, I, I, I, ctypes.POINTER(ctypes.c_size_t)]
         lib.aba_workspace_size.restype = I
+        IPt = ctypes.POINTER(ctypes.c_int)
+        LLP = ctypes.POINTER(ctypes.c_longlong)
+        lib.rd_fleet_create.argtypes = [I, IPt, D, D, D, ctypes.POINTER(P)]
+        lib.rd_fleet_create.restype = I
+        lib.rd_fleet_destroy.argtypes = [P]
+        lib.rd_fleet_destroy.restype = None
+        lib.rd_plan_create.argtypes = [P, I, IPt, IPt, I, ctypes.POINTER(P)]
+        lib.rd_plan_create.restype = I
+        lib.rd_plan_destroy.argtypes = [P]
+        lib.rd_plan_destroy.restype = None
+        lib.rd_plan_total_joints.argtypes = [P]
+        lib.rd_plan_total_joints.restype = ctypes.c_longlong
+        lib.rd_plan_offsets.argtypes = [P, LLP]
+        lib.rd_plan_offsets.restype = I
+        lib.rd_plan_groups.argtypes = [P]
+        lib.rd_plan_groups.restype = I
+        lib.fleet_batch.argtypes = [P, P, P, P, P, D, P, I, I, P]
+        lib.fleet_batch.restype = I
         lib.rd_measure_fma_peak.argtypes = [I, D, P]
         lib.rd_measure_fma_peak.restype = I
         _lib = lib
@@ -349,3 +367,112 @@ def aba(model, q, qd, tau, base=None, workspace=None, status=None, out=None, str
                           ctypes.c_void_p(stream.cuda_stream)))
     del keep
     return qdd
+
+
+RD_REQ_ID = 0
+RD_REQ_FD = 1
+RD_SCHED_PERSISTENT = 0
+RD_SCHED_PER_GROUP = 1
+
+
+def RD_FLEET_TUNE(log2_threads, ctas_per_sm):
+    return (int(log2_threads) << 8) | int(ctas_per_sm)
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+class Fleet:
+    """Many chains of different lengths on the current device (rd_fleet_create)."""
+
+    def __init__(self, chains):
+        lib = load()
+        self.n = np.ascontiguousarray([c.n for c in chains], dtype=np.int32)
+        self._M = np.ascontiguousarray(np.concatenate([c.M for c in chains]), dtype=np.float64)
+        self._S = np.ascontiguousarray(np.concatenate([c.S for c in chains]), dtype=np.float64)
+        self._J = np.ascontiguousarray(np.concatenate([c.inertia for c in chains]), dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(lib.rd_fleet_create(len(chains), _iptr(self.n), _dptr(self._M), _dptr(self._S),
+                                   _dptr(self._J), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.rd_fleet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A fixed request set on a fleet (rd_plan_create): robots[R], kinds[R] (RD_REQ_*)."""
+
+    def __init__(self, fleet, robots, kinds, dtype="float32"):
+        lib = load()
+        self.fleet = fleet
+        self.robots = np.ascontiguousarray(robots, dtype=np.int32)
+        self.kinds = np.ascontiguousarray(kinds, dtype=np.int32)
+        self.R = int(self.robots.shape[0])
+        self.dtype = dtype
+        h = ctypes.c_void_p()
+        _check(lib.rd_plan_create(fleet.handle, self.R, _iptr(self.robots), _iptr(self.kinds),
+                                  RD_F32 if dtype == "float32" else RD_F64, ctypes.byref(h)))
+        self._h = h
+        self.total_joints = int(lib.rd_plan_total_joints(h))
+        self.offsets = np.empty(self.R, dtype=np.int64)
+        _check(lib.rd_plan_offsets(h, self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
+        self.groups = int(lib.rd_plan_groups(h))
+        self.lengths = fleet.n[self.robots]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.rd_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fleet_batch(plan, q, qd, in2, out=None, base=None, status=None,
+                schedule=RD_SCHED_PERSISTENT, tune=0, stream=None):
+    """Evaluate every request of ``plan`` (fleet_batch). q, qd, in2: 1-D CUDA tensors
+    of plan.total_joints elements, request r at [offsets[r], offsets[r] + n_r);
+    in2 holds qdd for inverse and tau for forward dynamics requests; returns out
+    (tau, resp. qdd, in the same layout)."""
+    import torch
+
+    for t in (q, qd, in2):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("fleet_batch expects contiguous CUDA tensors")
+        if t.numel() != plan.total_joints:
+            raise ValueError(f"expected {plan.total_joints} joint values, got {t.numel()}")
+        want = torch.float32 if plan.dtype == "float32" else torch.float64
+        if t.dtype != want:
+            raise TypeError(f"plan dtype is {plan.dtype}")
+    if out is None:
+        out = torch.empty_like(q)
+    if stream is None:
+        stream = torch.cuda.current_stream(q.device)
+    keep, bp = _base_arg(base)
+    st_ptr = status.data_ptr() if status is not None else None
+    _check(_lib.fleet_batch(plan.handle, q.data_ptr(), qd.data_ptr(), in2.data_ptr(),
+                            out.data_ptr(), bp, st_ptr, int(schedule), int(tune),
+                            ctypes.c_void_p(stream.cuda_stream)))
+    del keep
+    return out

@@ -138,6 +138,10 @@ __device__ __forceinline__ Abi link_inertia(const double *Lc)
     return J;
 }
 
+// Workspace addressing: element (link i, component k) of an instance sits at
+// ws[(i * K + k) * stride + b]. A batch of one chain uses stride = B and the
+// instance index b (component-major, coalesced across threads); a request of a
+// fleet uses its own region with stride = 1, b = 0.
 template <typename T>
 __device__ __forceinline__ void aba_put(T *ws, int B, int b, int i, int k, T v)
 {
@@ -165,32 +169,17 @@ __device__ __forceinline__ Z aba_zget(const Z *ws, int B, int b, int i, int k)
     return ws[((size_t)i * kAbaSolveScalars + k) * (size_t)B + b];
 }
 
-// Shared memory: n * 24 constants in T, then n * 24 in FP64.
-// Z: arithmetic of the z_hat / lambda recursions and storage of U, c_hat,
-// 1/Omega (double by default; T when the caller asks for the spatial scans in
-// the data precision).
-template <typename T, typename Z, int BLOCK, bool VEC>
-__global__ void __launch_bounds__(BLOCK)
-aba_kernel(const T *__restrict__ consts, const double *__restrict__ consts64, int n, int B,
-           const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
-           T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
-           Z *__restrict__ wsz, BaseParams<T> base)
+// One forward-dynamics instance. sc / sd: the chain's constants (T and FP64,
+// shared or global memory); qr, qdr, taur, qddr: its joint rows; ws / wsz and
+// (B, b): its workspace (see aba_put). Returns 1 when an Omega_i <= 0 or a
+// non-finite qdd appeared.
+template <typename T, typename Z, bool VEC>
+__device__ __forceinline__ int aba_instance(const T *sc, const double *sd, int n,
+                                            const T *__restrict__ qr, const T *__restrict__ qdr,
+                                            const T *__restrict__ taur, T *__restrict__ qddr,
+                                            T *__restrict__ ws, Z *__restrict__ wsz, int B, int b,
+                                            const BaseParams<T> &base)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *sc = reinterpret_cast<T *>(smem);
-    double *sd = reinterpret_cast<double *>(smem + (((size_t)n * kLinkConsts * sizeof(T) + 15) & ~(size_t)15));
-    const int nc = n * kLinkConsts;
-    for (int k = threadIdx.x; k < nc; k += BLOCK) {
-        sc[k] = consts[k];
-        sd[k] = consts64[k];
-    }
-    __syncthreads();
-
-    const int b = blockIdx.x * BLOCK + threadIdx.x;
-    if (b >= B) return;
-    const size_t row = (size_t)b * (size_t)n;
-    const T *qr = q + row, *qdr = qd + row, *taur = tau + row;
-    T *qddr = qdd_out + row;
     int bad = 0;
 
     // ---- sweep 1: bias motion (qdd = 0) and bias wrenches
@@ -360,6 +349,36 @@ aba_kernel(const T *__restrict__ consts, const double *__restrict__ consts64, in
         }
         st_chunk<T, VEC>(qddr, i0, n, out);
     }
+    return bad;
+}
+
+
+// Shared memory: n * 24 constants in T, then n * 24 in FP64.
+// Z: arithmetic of the z_hat / lambda recursions and storage of U, c_hat,
+// 1/Omega (double by default; T when the caller asks for the spatial scans in
+// the data precision).
+template <typename T, typename Z, int BLOCK, bool VEC>
+__global__ void __launch_bounds__(BLOCK)
+aba_kernel(const T *__restrict__ consts, const double *__restrict__ consts64, int n, int B,
+           const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
+           T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
+           Z *__restrict__ wsz, BaseParams<T> base)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *sc = reinterpret_cast<T *>(smem);
+    double *sd = reinterpret_cast<double *>(smem + (((size_t)n * kLinkConsts * sizeof(T) + 15) & ~(size_t)15));
+    const int nc = n * kLinkConsts;
+    for (int k = threadIdx.x; k < nc; k += BLOCK) {
+        sc[k] = consts[k];
+        sd[k] = consts64[k];
+    }
+    __syncthreads();
+
+    const int b = blockIdx.x * BLOCK + threadIdx.x;
+    if (b >= B) return;
+    const size_t row = (size_t)b * (size_t)n;
+    const int bad = aba_instance<T, Z, VEC>(sc, sd, n, q + row, qd + row, tau + row, qdd_out + row,
+                                            ws, wsz, B, b, base);
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }
 

@@ -1,0 +1,307 @@
+// rdyn_fleet.cu -- many chains of different lengths, mixed inverse / forward
+// dynamics requests in one call (rd_fleet_*, rd_plan_*, fleet_batch).
+// All allocation happens when fleets and plans are created.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "fleet.cuh"
+#include "rdyn_internal.h"
+
+struct rd_fleet {
+    int device = 0;
+    int nrobots = 0;
+    long long total_links = 0;
+    std::vector<int> n;  // host copy
+    float *c32 = nullptr;
+    double *c64 = nullptr;
+    int *robot_n = nullptr, *robot_link = nullptr;
+    float *tn32 = nullptr;
+    double *tn64 = nullptr;
+};
+
+struct rd_plan {
+    const rd_fleet *fleet = nullptr;
+    int dtype = RD_F32;
+    int R = 0;
+    long long total_joints = 0;
+    std::vector<long long> off;               // user order
+    std::vector<std::pair<int, int>> groups;  // sorted positions [begin, end) of equal (kind, n)
+    int *order = nullptr, *req_robot = nullptr, *req_kind = nullptr, *counter = nullptr;
+    long long *req_off = nullptr, *req_ws = nullptr;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int sms = 0;
+    // side streams for RD_SCHED_PER_GROUP (fork / join through events)
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
+};
+
+namespace {
+
+template <typename X>
+cudaError_t upload(X **dst, const X *src, size_t count)
+{
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(count, 1) * sizeof(X));
+    if (e == cudaSuccess && count) e = cudaMemcpy(*dst, src, count * sizeof(X), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+extern "C" void rd_fleet_destroy(rd_fleet *f)
+{
+    if (!f) return;
+    cudaFree(f->c32);
+    cudaFree(f->c64);
+    cudaFree(f->robot_n);
+    cudaFree(f->robot_link);
+    cudaFree(f->tn32);
+    cudaFree(f->tn64);
+    delete f;
+}
+
+extern "C" int rd_fleet_create(int nrobots, const int *n, const double *M, const double *S,
+                               const double *inertia, rd_fleet **out)
+{
+    g_rd_error.clear();
+    if (!out) return rd_fail(RD_ERR_ARG, "rd_fleet_create: out is null");
+    *out = nullptr;
+    if (nrobots < 1) return rd_fail(RD_ERR_RANGE, "rd_fleet_create: nrobots = %d", nrobots);
+    if (!n || !M || !S || !inertia) return rd_fail(RD_ERR_ARG, "rd_fleet_create: null array");
+    std::vector<double> all64;
+    std::vector<int> link(nrobots);
+    std::vector<double> tn((size_t)nrobots * 12);
+    long long lo = 0;
+    for (int r = 0; r < nrobots; ++r) {
+        if (n[r] < 1 || n[r] > RD_MAX_LINKS)
+            return rd_fail(RD_ERR_RANGE, "rd_fleet_create: robot %d has n = %d outside [1, %d]", r,
+                           n[r], RD_MAX_LINKS);
+        std::vector<double> c;
+        double TnR[9], Tnp[3];
+        int rc = rd_build_chain(n[r], M + 12 * lo, S + 6 * lo, inertia + 10 * lo, c, TnR, Tnp);
+        if (rc) {
+            std::string msg = g_rd_error;
+            return rd_fail(rc, "rd_fleet_create: robot %d: %s", r, msg.c_str());
+        }
+        link[r] = (int)lo;
+        all64.insert(all64.end(), c.begin(), c.end());
+        for (int k = 0; k < 9; ++k) tn[(size_t)r * 12 + k] = TnR[k];
+        for (int k = 0; k < 3; ++k) tn[(size_t)r * 12 + 9 + k] = Tnp[k];
+        lo += n[r];
+    }
+    rd_fleet *f = new (std::nothrow) rd_fleet();
+    if (!f) return rd_fail(RD_ERR_ALLOC, "rd_fleet_create: host allocation failed");
+    f->nrobots = nrobots;
+    f->total_links = lo;
+    f->n.assign(n, n + nrobots);
+    cudaError_t e = cudaGetDevice(&f->device);
+    std::vector<float> all32(all64.begin(), all64.end());
+    std::vector<float> tn32(tn.begin(), tn.end());
+    if (e == cudaSuccess) e = upload(&f->c64, all64.data(), all64.size());
+    if (e == cudaSuccess) e = upload(&f->c32, all32.data(), all32.size());
+    if (e == cudaSuccess) e = upload(&f->robot_n, n, (size_t)nrobots);
+    if (e == cudaSuccess) e = upload(&f->robot_link, link.data(), link.size());
+    if (e == cudaSuccess) e = upload(&f->tn64, tn.data(), tn.size());
+    if (e == cudaSuccess) e = upload(&f->tn32, tn32.data(), tn32.size());
+    if (e != cudaSuccess) {
+        rd_fleet_destroy(f);
+        return rd_fail(RD_ERR_ALLOC, "rd_fleet_create: %s", cudaGetErrorString(e));
+    }
+    *out = f;
+    return RD_OK;
+}
+
+extern "C" void rd_plan_destroy(rd_plan *p)
+{
+    if (!p) return;
+    cudaFree(p->order);
+    cudaFree(p->req_robot);
+    cudaFree(p->req_kind);
+    cudaFree(p->counter);
+    cudaFree(p->req_off);
+    cudaFree(p->req_ws);
+    cudaFree(p->ws);
+    for (int k = 0; k < rd_plan::kSide; ++k) {
+        if (p->side[k]) cudaStreamDestroy(p->side[k]);
+        if (p->join[k]) cudaEventDestroy(p->join[k]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
+    delete p;
+}
+
+extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const int *kind,
+                              int dtype, rd_plan **out)
+{
+    g_rd_error.clear();
+    if (!out) return rd_fail(RD_ERR_ARG, "rd_plan_create: out is null");
+    *out = nullptr;
+    if (!f || !robot || !kind) return rd_fail(RD_ERR_ARG, "rd_plan_create: null argument");
+    if (R < 1) return rd_fail(RD_ERR_RANGE, "rd_plan_create: R = %d", R);
+    if (dtype != RD_F32 && dtype != RD_F64) return rd_fail(RD_ERR_DTYPE, "rd_plan_create: dtype %d", dtype);
+    const size_t esz = dtype == RD_F32 ? 4 : 8;
+    std::vector<long long> off(R), wsoff(R, 0);
+    long long tot = 0;
+    for (int r = 0; r < R; ++r) {
+        if (robot[r] < 0 || robot[r] >= f->nrobots)
+            return rd_fail(RD_ERR_ARG, "rd_plan_create: request %d names robot %d", r, robot[r]);
+        if (kind[r] != RD_REQ_ID && kind[r] != RD_REQ_FD)
+            return rd_fail(RD_ERR_ARG, "rd_plan_create: request %d has kind %d", r, kind[r]);
+        off[r] = tot;
+        tot += f->n[robot[r]];
+    }
+    // forward dynamics first (heavier), then longer chains first
+    std::vector<int> order(R);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (kind[a] != kind[b]) return kind[a] > kind[b];
+        return f->n[robot[a]] > f->n[robot[b]];
+    });
+    size_t ws = 0;
+    for (int k = 0; k < R; ++k) {
+        const int r = order[k];
+        if (kind[r] != RD_REQ_FD) continue;
+        const size_t nl = (size_t)f->n[robot[r]];
+        wsoff[r] = (long long)ws;
+        ws += ((nl * 10 * esz + 15) & ~(size_t)15) + ((nl * 8 * 8 + 15) & ~(size_t)15);
+    }
+    rd_plan *p = new (std::nothrow) rd_plan();
+    if (!p) return rd_fail(RD_ERR_ALLOC, "rd_plan_create: host allocation failed");
+    p->fleet = f;
+    p->dtype = dtype;
+    p->R = R;
+    p->total_joints = tot;
+    p->off = off;
+    for (int k = 0; k < R;) {
+        int j = k;
+        const int r0 = order[k];
+        while (j < R && kind[order[j]] == kind[r0] && f->n[robot[order[j]]] == f->n[robot[r0]]) ++j;
+        p->groups.emplace_back(k, j);
+        k = j;
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, f->device);
+    if (e == cudaSuccess) e = upload(&p->order, order.data(), order.size());
+    if (e == cudaSuccess) e = upload(&p->req_robot, robot, (size_t)R);
+    if (e == cudaSuccess) e = upload(&p->req_kind, kind, (size_t)R);
+    if (e == cudaSuccess) e = upload(&p->req_off, off.data(), off.size());
+    if (e == cudaSuccess) e = upload(&p->req_ws, wsoff.data(), wsoff.size());
+    if (e == cudaSuccess) e = cudaMalloc(&p->counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->ws, std::max<size_t>(ws, 16));
+    p->ws_bytes = ws;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+    for (int k = 0; k < rd_plan::kSide && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        rd_plan_destroy(p);
+        return rd_fail(RD_ERR_ALLOC, "rd_plan_create: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return RD_OK;
+}
+
+extern "C" long long rd_plan_total_joints(const rd_plan *p) { return p ? p->total_joints : -1; }
+
+extern "C" int rd_plan_offsets(const rd_plan *p, long long *off)
+{
+    if (!p || !off) return rd_fail(RD_ERR_ARG, "rd_plan_offsets: null argument");
+    std::copy(p->off.begin(), p->off.end(), off);
+    return RD_OK;
+}
+
+extern "C" int rd_plan_groups(const rd_plan *p) { return p ? (int)p->groups.size() : -1; }
+
+namespace {
+
+template <typename T>
+int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, void *out,
+              const double *b18, int *status, int schedule, int tune, cudaStream_t s)
+{
+    const rd_fleet *f = p->fleet;
+    rdyn::FleetArgs<T> a;
+    if constexpr (sizeof(T) == 4) {
+        a.consts = f->c32;
+        a.robot_tn = f->tn32;
+    } else {
+        a.consts = f->c64;
+        a.robot_tn = f->tn64;
+    }
+    a.consts64 = f->c64;
+    a.robot_n = f->robot_n;
+    a.robot_link = f->robot_link;
+    a.order = p->order;
+    a.req_robot = p->req_robot;
+    a.req_kind = p->req_kind;
+    a.req_off = p->req_off;
+    a.req_ws = p->req_ws;
+    a.R = p->R;
+    a.q = static_cast<const T *>(q);
+    a.qd = static_cast<const T *>(qd);
+    a.in2 = static_cast<const T *>(in2);
+    a.out = static_cast<T *>(out);
+    a.status = status;
+    a.ws = p->ws;
+    a.counter = p->counter;
+    for (int k = 0; k < 6; ++k) {
+        a.base.V0[k] = (T)b18[k];
+        a.base.dV0[k] = (T)b18[6 + k];
+        a.base.Fn[k] = (T)b18[12 + k];
+    }
+    cudaError_t e = cudaSuccess;
+    if (schedule == RD_SCHED_PERSISTENT) {
+        int threads = (tune >> 8) & 0xff ? 1 << ((tune >> 8) & 0xff) : 128;
+        int per_sm = tune & 0xff ? tune & 0xff : 4;
+        if (threads < 32 || threads > 1024)
+            return rd_fail(RD_ERR_ARG, "fleet_batch: %d threads per block", threads);
+        e = cudaMemsetAsync(p->counter, 0, sizeof(int), s);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch: counter reset");
+        rdyn::fleet_persistent_kernel<T><<<p->sms * per_sm, threads, 0, s>>>(a);
+    } else if (schedule == RD_SCHED_PER_GROUP) {
+        // one launch per group, spread over side streams that fork from and
+        // join back into the caller's stream (so groups can run concurrently)
+        e = cudaEventRecord(p->fork, s);
+        for (int k = 0; k < rd_plan::kSide && e == cudaSuccess; ++k)
+            e = cudaStreamWaitEvent(p->side[k], p->fork, 0);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch: fork");
+        int k = 0;
+        for (const auto &g : p->groups) {
+            const int len = g.second - g.first;
+            rdyn::fleet_range_kernel<T><<<(len + 127) / 128, 128, 0, p->side[k]>>>(a, g.first, g.second);
+            k = (k + 1) % rd_plan::kSide;
+        }
+        for (int j = 0; j < rd_plan::kSide && e == cudaSuccess; ++j) {
+            e = cudaEventRecord(p->join[j], p->side[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join[j], 0);
+        }
+        if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch: join");
+    } else {
+        return rd_fail(RD_ERR_ARG, "fleet_batch: unknown schedule %d", schedule);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch launch");
+    return RD_OK;
+}
+
+}  // namespace
+
+extern "C" int fleet_batch(const rd_plan *p, const void *q, const void *qd, const void *in2,
+                           void *out, const double *base, int *status, int schedule, int tune,
+                           void *stream)
+{
+    g_rd_error.clear();
+    if (!p) return rd_fail(RD_ERR_ARG, "fleet_batch: null plan");
+    if (!q || !qd || !in2 || !out) return rd_fail(RD_ERR_ARG, "fleet_batch: null data pointer");
+    if (out == q || out == qd || out == in2)
+        return rd_fail(RD_ERR_ARG, "fleet_batch: out aliases an input");
+    static const double dflt[18] = {0, 0, 0, 0, 0, 0, 0, 0, 9.81, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double *b18 = base ? base : dflt;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->dtype == RD_F32) return run_fleet<float>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+    return run_fleet<double>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+}

@@ -49,3 +49,5 @@ int rd_aba_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd,
                         int flags, cudaStream_t s);
 size_t rd_aba_ws_bytes_f32(int n, int B, int flags);
 size_t rd_aba_ws_bytes_f64(int n, int B, int flags);
+int rd_build_chain(int n, const double *M, const double *S, const double *inertia,
+                   std::vector<double> &c64, double TnR[9], double Tnp[3]);

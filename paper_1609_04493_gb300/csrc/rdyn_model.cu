@@ -138,16 +138,14 @@ extern "C" int rd_model_links(const rd_model *m)
     return m->n;
 }
 
-extern "C" int rd_model_create(int n, const double *M, const double *S, const double *inertia,
-                               rd_model **out)
+// Joint-frame constants of one chain (24 doubles per link, see spatial.cuh) and
+// the joint frame of its last link (for F_{n+1}). Host-side, FP64.
+int rd_build_chain(int n, const double *M, const double *S, const double *inertia,
+                   std::vector<double> &c64, double TnR[9], double Tnp[3])
 {
-    g_rd_error.clear();
-    if (!out) return rd_fail(RD_ERR_ARG, "rd_model_create: out is null");
-    *out = nullptr;
     if (n < 1 || n > RD_MAX_LINKS)
-        return rd_fail(RD_ERR_RANGE, "rd_model_create: n = %d outside [1, %d]", n, RD_MAX_LINKS);
-    if (!M || !S || !inertia) return rd_fail(RD_ERR_ARG, "rd_model_create: null model array");
-
+        return rd_fail(RD_ERR_RANGE, "n = %d outside [1, %d]", n, RD_MAX_LINKS);
+    if (!M || !S || !inertia) return rd_fail(RD_ERR_ARG, "null model array");
     std::vector<Rigid> T(n + 1);
     for (int k = 0; k < 9; ++k) T[0].R[k] = (k % 4 == 0) ? 1.0 : 0.0;
     T[0].p[0] = T[0].p[1] = T[0].p[2] = 0.0;
@@ -155,8 +153,7 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
         int rc = joint_frame(i, S + 6 * i, T[i + 1]);
         if (rc) return rc;
     }
-
-    std::vector<double> c64((size_t)n * rdyn::kLinkConsts, 0.0);
+    c64.assign((size_t)n * rdyn::kLinkConsts, 0.0);
     for (int i = 0; i < n; ++i) {
         const double *in = inertia + 10 * i;
         double m = in[0];
@@ -201,6 +198,24 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
         o[20] = 0.5 * (Ip[0][2] + Ip[2][0]);
         o[21] = 0.5 * (Ip[1][2] + Ip[2][1]);
     }
+    for (int k = 0; k < 9; ++k) TnR[k] = T[n].R[k];
+    for (int k = 0; k < 3; ++k) Tnp[k] = T[n].p[k];
+    return RD_OK;
+}
+
+extern "C" int rd_model_create(int n, const double *M, const double *S, const double *inertia,
+                               rd_model **out)
+{
+    g_rd_error.clear();
+    if (!out) return rd_fail(RD_ERR_ARG, "rd_model_create: out is null");
+    *out = nullptr;
+    if (n < 1 || n > RD_MAX_LINKS)
+        return rd_fail(RD_ERR_RANGE, "rd_model_create: n = %d outside [1, %d]", n, RD_MAX_LINKS);
+    if (!M || !S || !inertia) return rd_fail(RD_ERR_ARG, "rd_model_create: null model array");
+    std::vector<double> c64;
+    double TnR[9], Tnp[3];
+    int rc = rd_build_chain(n, M, S, inertia, c64, TnR, Tnp);
+    if (rc) return rc;
 
     rd_model *mdl = new (std::nothrow) rd_model();
     if (!mdl) return rd_fail(RD_ERR_ALLOC, "rd_model_create: host allocation failed");
@@ -210,8 +225,8 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
         delete mdl;
         return rd_cuda_fail(e, "cudaGetDevice");
     }
-    for (int k = 0; k < 9; ++k) mdl->TnR[k] = T[n].R[k];
-    for (int k = 0; k < 3; ++k) mdl->Tnp[k] = T[n].p[k];
+    for (int k = 0; k < 9; ++k) mdl->TnR[k] = TnR[k];
+    for (int k = 0; k < 3; ++k) mdl->Tnp[k] = Tnp[k];
     mdl->host_c64 = c64;
 
     std::vector<float> c32(c64.size());

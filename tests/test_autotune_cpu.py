@@ -1,0 +1,23 @@
+"""Host-side logic of the autotuner: cache round trip and candidate lists."""
+from paper_1609_04493_gb300 import autotune, binding as b
+
+
+def test_cache_round_trip(tmp_path, monkeypatch):
+    monkeypatch.setenv("RDYN_TUNE_CACHE", str(tmp_path / "sub" / "tune.json"))
+    autotune._store("k1", {"variant": 3})
+    autotune._store("k2", {"variant": 5})
+    c = autotune._load_cache()
+    assert c["k1"]["variant"] == 3 and c["k2"]["variant"] == 5
+
+
+def test_rnea_candidates_respect_lane_capacity():
+    for n in (1, 16, 40, 100, 128):
+        for v in autotune.rnea_candidates(n, 1024, None):
+            if (v & 0xf00) == 0x100:
+                assert n <= 8 * (v & 0xff)
+
+
+def test_fleet_candidates_fit_a_cta():
+    for sched, tune in autotune.fleet_candidates():
+        if sched == b.RD_SCHED_PERSISTENT:
+            assert (1 << (tune >> 8)) * (tune & 0xff) <= 1024

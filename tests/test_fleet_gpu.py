@@ -1,0 +1,121 @@
+"""GPU parity of fleet_batch: mixed inverse / forward dynamics requests over
+many chains of different lengths, each request with its own robot, in one
+persistent launch or one launch per (kind, n) group, against the FP64 oracle.
+Bars as for rnea_batch (ID) and aba_batch (FD)."""
+import numpy as np
+import pytest
+
+import chaingen
+import oracle
+
+pytestmark = pytest.mark.gpu
+TOL_ID = {"float32": 1e-4, "float64": 1e-10}
+TOL_FD = {"float32": 1e-3, "float64": 1e-8}
+
+
+def build(rd, count, n_lo, n_hi, dtype, seed=7, fd_fraction=0.2):
+    import torch
+
+    reqs = chaingen.uneven_requests(count, n_lo=n_lo, n_hi=n_hi, fd_fraction=fd_fraction, seed=seed)
+    fleet = rd.Fleet([r["chain"] for r in reqs])
+    kinds = np.array([1 if r["kind"] == "fd" else 0 for r in reqs], dtype=np.int32)
+    plan = rd.Plan(fleet, np.arange(count, dtype=np.int32), kinds, dtype=dtype)
+    J = plan.total_joints
+    rng = np.random.default_rng(seed + 1)
+    q = rng.uniform(-np.pi, np.pi, J)
+    qd = rng.normal(0, 1, J)
+    in2 = np.where(np.repeat(kinds, plan.lengths) == 1, rng.normal(0, 10, J), rng.normal(0, 2, J))
+    npdt = np.float32 if dtype == "float32" else np.float64
+    host = [x.astype(npdt) for x in (q, qd, in2)]
+    dev = [torch.from_numpy(x).cuda() for x in host]
+    return reqs, fleet, plan, kinds, [x.astype(np.float64) for x in host], dev
+
+
+def check(reqs, plan, kinds, host, out, dtype, sample=None):
+    idx = range(len(reqs)) if sample is None else sample
+    worst_id = worst_fd = 0.0
+    for r in idx:
+        o, n = plan.offsets[r], plan.lengths[r]
+        sl = slice(o, o + n)
+        ch = reqs[r]["chain"]
+        if kinds[r] == 0:
+            ref = oracle.rnea(ch, host[0][sl][None], host[1][sl][None], host[2][sl][None])
+            worst_id = max(worst_id, oracle.rel_err(out[sl][None], ref))
+        else:
+            ref = oracle.fd_aba(ch, host[0][sl][None], host[1][sl][None], host[2][sl][None])
+            worst_fd = max(worst_fd, oracle.rel_err(out[sl][None], ref))
+    assert worst_id <= TOL_ID[dtype], worst_id
+    assert worst_fd <= TOL_FD[dtype], worst_fd
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_fleet_mixed_requests(cuda_lib, dtype, schedule):
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 400, 1, 40, dtype, fd_fraction=0.3)
+    out = cuda_lib.fleet_batch(plan, *dev, schedule=schedule).cpu().numpy().astype(np.float64)
+    check(reqs, plan, kinds, host, out, dtype)
+
+
+def test_fleet_schedules_and_shapes_agree_exactly(cuda_lib):
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 300, 6, 60, "float32", seed=9)
+    ref = cuda_lib.fleet_batch(plan, *dev, schedule=1).cpu().numpy()
+    for tune in (0, cuda_lib.RD_FLEET_TUNE(5, 1), cuda_lib.RD_FLEET_TUNE(8, 2)):
+        out = cuda_lib.fleet_batch(plan, *dev, schedule=0, tune=tune).cpu().numpy()
+        assert np.array_equal(out, ref)
+
+
+def test_fleet_uneven_workload_sampled(cuda_lib):
+    """5000 requests, n uniform in 6..100, 80% ID / 20% FD, FP32: a sample of 250
+    requests checked against the oracle."""
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 5000, 6, 100, "float32", seed=1609)
+    out = cuda_lib.fleet_batch(plan, *dev).cpu().numpy().astype(np.float64)
+    check(reqs, plan, kinds, host, out, "float32", sample=range(0, 5000, 20))
+
+
+def test_fleet_base_motion_and_wrench(cuda_lib):
+    import torch
+
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 60, 2, 20, "float64", seed=5, fd_fraction=0.5)
+    out = cuda_lib.fleet_batch(plan, *dev, base=base).cpu().numpy()
+    for r in range(60):
+        o, n = plan.offsets[r], plan.lengths[r]
+        sl = slice(o, o + n)
+        fn = oracle.rnea if kinds[r] == 0 else oracle.fd_aba
+        ref = fn(reqs[r]["chain"], host[0][sl][None], host[1][sl][None], host[2][sl][None], base=base)
+        assert oracle.rel_err(out[sl][None], ref) <= (TOL_ID if kinds[r] == 0 else TOL_FD)["float64"]
+
+
+def test_fleet_status_flags_singular_forward_request(cuda_lib):
+    import torch
+
+    chains = [chaingen.pendulum(1.0, 0.0, 0.0), chaingen.make_chain(5)]
+    fleet = cuda_lib.Fleet(chains)
+    plan = cuda_lib.Plan(fleet, [0, 1, 1], [1, 1, 0], dtype="float64")
+    J = plan.total_joints
+    x = torch.zeros(J, dtype=torch.float64, device="cuda")
+    status = torch.full((3,), -1, dtype=torch.int32, device="cuda")
+    cuda_lib.fleet_batch(plan, x, x, x + 1.0, status=status)
+    assert status.cpu().tolist()[:2] == [1, 0]
+
+
+def test_autotuner_picks_a_working_configuration(cuda_lib, tmp_path, monkeypatch):
+    import torch
+
+    from paper_1609_04493_gb300 import autotune
+
+    monkeypatch.setenv("RDYN_TUNE_CACHE", str(tmp_path / "tune.json"))
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 200, 6, 30, "float32", seed=3)
+    (sched, tune), times = autotune.tune_fleet(plan, *dev, use_cache=False)
+    assert (sched, tune) in times and len(times) == len(autotune.fleet_candidates())
+    again, _ = autotune.tune_fleet(plan, *dev)  # from the cache now
+    assert again == (sched, tune)
+    ch = chaingen.make_chain(16)
+    model = cuda_lib.Model(ch)
+    st = chaingen.make_states(2048, 16, seed=4)
+    x = [torch.from_numpy(st[k]).float().cuda() for k in ("q", "qd", "qdd")]
+    v, t = autotune.tune_rnea(model, *x, use_cache=False)
+    tau = cuda_lib.rnea(model, *x, variant=v).cpu().numpy()
+    ref = oracle.rnea(ch, *(a.cpu().double().numpy() for a in x))
+    assert oracle.rel_err(tau, ref) <= 1e-4
