@@ -51,8 +51,11 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
-    p.add_argument("--kernel-only", choices=["f32", "f64"], default=None,
-                   help="profiling case: W + K plain launches of the headline kernel, no JSON")
+    p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
+    p.add_argument("--kernel-only", choices=["f32", "f64", "vjp", "aba", "fleet"], default=None,
+                   help="profiling case: W + K plain launches of one kernel, no JSON "
+                        "(f32/f64: RNEA n=32 B=65536; vjp: adjoint n=32 B=8192; "
+                        "aba: forward dynamics n=64 B=16384; fleet: 20000 mixed requests)")
     return p.parse_args()
 
 
@@ -213,6 +216,112 @@ def capture(torch, rd, model, sets, count, variant=0):
     return g
 
 
+def capture_calls(torch, fn, count):
+    """CUDA graph of `count` calls of fn(k)."""
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn(0)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            for k in range(count):
+                fn(k)
+    torch.cuda.synchronize()
+    return g
+
+
+def time_calls(torch, fn, steps, warmup, dist, sampler):
+    gw = capture_calls(torch, fn, max(warmup, 1))
+    gw.replay()
+    torch.cuda.synchronize()
+    g = capture_calls(torch, fn, steps)
+    return max_over_ranks(dist, timed_graph(torch, g, dist, sampler))
+
+
+def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
+    out = {}
+    for B, mode in ((8192, rd.RD_VJP_RECOMPUTE), (262144, rd.RD_VJP_RECOMPUTE),
+                    (8192, rd.RD_VJP_STORE)):
+        sets = []
+        nsets = 2 if B > 100000 else 8
+        for r in range(nsets):
+            st = chaingen.make_states(B, N_LINKS, seed=5000 + r, kinds=("q", "qd", "qdd", "w"))
+            x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]
+            sets.append((x, tuple(torch.empty_like(x[0]) for _ in range(3))))
+        ws = None
+        if mode == rd.RD_VJP_STORE:
+            ws = torch.empty(rd.vjp_workspace_bytes(model, B, 0), dtype=torch.uint8, device=dev)
+        steps = max(3, min(K, 200 if B < 100000 else 50))
+
+        def call(k):
+            x, o = sets[k % len(sets)]
+            rd.rnea_vjp(model, *x, mode=mode, workspace=ws, out=o)
+
+        t = time_calls(torch, call, steps, 3, dist, sampler)
+        name = f"B{B}_{'store' if mode == rd.RD_VJP_STORE else 'recompute'}"
+        out[name] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
+                     "steps": steps}
+    out["metric"] = "RNEA adjoint d(w^T tau)/d(q, qd, qdd) evals/s, n=32 FP32"
+    return out
+
+
+def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
+    out = {}
+    B = 16384
+    for n in (16, 64):
+        model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
+        sets = []
+        for r in range(4):
+            st = chaingen.make_states(B, n, seed=6000 + r, kinds=("q", "qd", "tau"))
+            sets.append([torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")])
+        ws = torch.empty(rd.aba_workspace_bytes(model, B, 0), dtype=torch.uint8, device=dev)
+        o = torch.empty_like(sets[0][0])
+        steps = max(3, min(K, 50))
+
+        def call(k):
+            x = sets[k % len(sets)]
+            rd.aba(model, *x, workspace=ws, out=o)
+
+        t = time_calls(torch, call, steps, 3, dist, sampler)
+        out[f"n{n}_B{B}"] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
+                             "steps": steps}
+    out["metric"] = ("forward dynamics (articulated-body, FP32 data, FP64 inertia updates and "
+                     "solves) evals/s")
+    return out
+
+
+def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
+    from paper_1609_04493_gb300 import autotune
+
+    reqs = chaingen.uneven_requests(count, n_lo=6, n_hi=100, fd_fraction=0.2, seed=chaingen.BASE_SEED)
+    fleet = rd.Fleet([r["chain"] for r in reqs])
+    kinds = np.array([1 if r["kind"] == "fd" else 0 for r in reqs], dtype=np.int32)
+    plan = rd.Plan(fleet, np.arange(count, dtype=np.int32), kinds, dtype="float32")
+    J = plan.total_joints
+    rng = np.random.default_rng(77)
+    fd_mask = np.repeat(kinds, plan.lengths) == 1
+    in2 = np.where(fd_mask, rng.normal(0, 10, J), rng.normal(0, 2, J))
+    x = [torch.from_numpy(a.astype(np.float32)).to(dev)
+         for a in (rng.uniform(-np.pi, np.pi, J), rng.normal(0, 1, J), in2)]
+    o = torch.empty_like(x[0])
+    (sched, tune), _ = autotune.tune_fleet(plan, *x, out=o)
+    steps = max(3, min(K, 20))
+    res = {}
+    for name, (sc, tu) in (("persistent_tuned", (sched, tune)),
+                           ("per_group_launches", (rd.RD_SCHED_PER_GROUP, 0))):
+        t = time_calls(torch, lambda k: rd.fleet_batch(plan, *x, out=o, schedule=sc, tune=tu),
+                       steps, 3, dist, sampler)
+        res[name] = {"value": count * steps / t, "unit": "requests/s",
+                     "ms_per_step": t / steps * 1e3, "steps": steps,
+                     "schedule": sc, "tune": tu}
+    res["workload"] = (f"{count} requests, own robot each, n uniform in 6..100 "
+                       f"({J} joints), {int(kinds.sum())} forward / {count - int(kinds.sum())} "
+                       f"inverse dynamics, FP32 (FP64 inertia updates and solves)")
+    res["launches_per_group_schedule"] = plan.groups
+    return res
+
+
 def timed_graph(torch, g, dist, sampler):
     barrier(dist)
     torch.cuda.synchronize()
@@ -315,7 +424,7 @@ def run_ours(args):
         out = torch.empty_like(host[0]).pin_memory()
         for _ in range(3):
             rd.rnea_host(model, *host, out=out)
-        Ke = max(3, min(K, 50))
+        Ke = max(3, min(K, 200))
         barrier(dist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -323,10 +432,21 @@ def run_ours(args):
             rd.rnea_host(model, *host, out=out)
         te = max_over_ranks(dist, time.perf_counter() - t0)
         barrier(dist)
+        if sampler is not None:
+            sampler.region(t0, t0 + te)
         res["e2e"] = {"value": world * BATCH * Ke / te, "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
                       "d2h_bytes_per_step": BATCH * N_LINKS * 4,
-                      "api": "rnea_batch_host (pinned host arrays, FP32)"}
+                      "api": "rnea_batch_host, pinned host arrays, FP32 (kernel reads and "
+                             "writes them in place over the host link)"}
+
+        # ---- adjoint (rnea_vjp), n = 32 FP32
+        res["adjoint"] = adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K)
+        # ---- forward dynamics (aba_batch), n = 16 and 64, B = 16384 FP32
+        res["forward_dynamics"] = fd_section(torch, rd, chaingen, dev, dist, sampler, K)
+        # ---- uneven batching: 100000 mixed requests (fleet_batch)
+        if not args.no_uneven:
+            res["uneven"] = uneven_section(torch, rd, chaingen, dev, dist, sampler, K)
 
     if sampler is not None:
         res["clocks"] = sampler.stop()
@@ -408,21 +528,50 @@ def run_reference(args):
 
 
 def run_kernel_only(args):
-    """Small profiling case for ncu: the headline launch, W + K times, no graph."""
+    """Small profiling cases for ncu: W + K plain launches of one kernel, no graph."""
     import torch
 
     import chaingen
     import paper_1609_04493_gb300 as rd
 
     rd.load()
-    dt = torch.float32 if args.kernel_only == "f32" else torch.float64
-    model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
-    x = make_inputs(torch, torch.device("cuda", 0), dt, 1, 1000)[0]
-    for _ in range(args.warmup + args.steps):
-        rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"])
+    dev = torch.device("cuda", 0)
+    calls = args.warmup + args.steps
+    if args.kernel_only in ("f32", "f64"):
+        dt = torch.float32 if args.kernel_only == "f32" else torch.float64
+        model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
+        x = make_inputs(torch, dev, dt, 1, 1000)[0]
+        for _ in range(calls):
+            rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"])
+        res = x["tau"]
+    elif args.kernel_only == "vjp":
+        model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
+        st = chaingen.make_states(8192, N_LINKS, seed=5000, kinds=("q", "qd", "qdd", "w"))
+        x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]
+        for _ in range(calls):
+            res = rd.rnea_vjp(model, *x, mode=rd.RD_VJP_RECOMPUTE)[0]
+    elif args.kernel_only == "aba":
+        model = rd.Model(chaingen.make_chain(64, seed=chaingen.BASE_SEED))
+        st = chaingen.make_states(16384, 64, seed=6000, kinds=("q", "qd", "tau"))
+        x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
+        ws = torch.empty(rd.aba_workspace_bytes(model, 16384, 0), dtype=torch.uint8, device=dev)
+        for _ in range(calls):
+            res = rd.aba(model, *x, workspace=ws)
+    else:
+        count = 20000
+        reqs = chaingen.uneven_requests(count, 6, 100, 0.2, seed=chaingen.BASE_SEED)
+        fleet = rd.Fleet([r["chain"] for r in reqs])
+        kinds = np.array([1 if r["kind"] == "fd" else 0 for r in reqs], dtype=np.int32)
+        plan = rd.Plan(fleet, np.arange(count, dtype=np.int32), kinds, "float32")
+        rng = np.random.default_rng(77)
+        J = plan.total_joints
+        x = [torch.from_numpy(a.astype(np.float32)).to(dev)
+             for a in (rng.uniform(-np.pi, np.pi, J), rng.normal(0, 1, J), rng.normal(0, 5, J))]
+        for _ in range(calls):
+            res = rd.fleet_batch(plan, *x, tune=rd.RD_FLEET_TUNE(7, 1))
     torch.cuda.synchronize()
-    print(f"kernel-only {args.kernel_only}: {args.warmup + args.steps} launches, "
-          f"max|tau| = {float(x['tau'].abs().max()):.4g}")
+    print(f"kernel-only {args.kernel_only}: {calls} launches, max|out| = "
+          f"{float(res.abs().max()):.4g}")
 
 
 def main():

@@ -28,6 +28,23 @@ extern "C" int rnea_batch(const rd_model *m, int B, int dtype, const void *q, co
     return rd_rnea_dispatch_f64(m, B, q, qd, qdd, tau, b18, variant, s);
 }
 
+namespace {
+
+// Device-visible address of a pinned (page-locked or registered) host buffer,
+// or nullptr when the pointer is not one.
+const void *pinned_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
+}  // namespace
+
 extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, const void *qd,
                                const void *qdd, void *tau, const double *base, int variant,
                                void *stream)
@@ -40,12 +57,25 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
     if (B == 0) return RD_OK;
     if (!q || !qd || !qdd || !tau)
         return rd_fail(RD_ERR_ARG, "rnea_batch_host: null batch pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    // Pinned host arrays: the kernel reads and writes them in place over the
+    // host link (coherent on Grace-Blackwell), no staging copies.
+    const void *dq = pinned_device_ptr(q), *dqd = pinned_device_ptr(qd),
+               *dqdd = pinned_device_ptr(qdd), *dtau = pinned_device_ptr(tau);
+    if (dq && dqd && dqdd && dtau) {
+        int rc = rnea_batch(m, B, dtype, dq, dqd, dqdd, const_cast<void *>(dtau), base, variant,
+                            stream);
+        if (rc) return rc;
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: synchronize");
+        return RD_OK;
+    }
+    // Otherwise stage through device buffers owned by the model.
     const size_t esz = dtype == RD_F32 ? 4 : 8;
     const size_t arr = (size_t)B * m->n * esz;
     const size_t slot = (arr + 255) & ~(size_t)255;
     std::lock_guard<std::mutex> lk(m->io_mu);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
     if (m->io_bytes < 4 * slot) {
         if (m->d_io) {
             e = cudaStreamSynchronize(s);
@@ -60,14 +90,14 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
         m->io_bytes = 4 * slot;
     }
     char *d = static_cast<char *>(m->d_io);
-    void *dq = d, *dqd = d + slot, *dqdd = d + 2 * slot, *dtau = d + 3 * slot;
-    e = cudaMemcpyAsync(dq, q, arr, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dqd, qd, arr, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dqdd, qdd, arr, cudaMemcpyHostToDevice, s);
+    void *sq = d, *sqd = d + slot, *sqdd = d + 2 * slot, *stau = d + 3 * slot;
+    e = cudaMemcpyAsync(sq, q, arr, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sqd, qd, arr, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sqdd, qdd, arr, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to device");
-    int rc = rnea_batch(m, B, dtype, dq, dqd, dqdd, dtau, base, variant, stream);
+    int rc = rnea_batch(m, B, dtype, sq, sqd, sqdd, stau, base, variant, stream);
     if (rc) return rc;
-    e = cudaMemcpyAsync(tau, dtau, arr, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(tau, stau, arr, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to host");
     return RD_OK;

@@ -154,6 +154,22 @@ def test_rnea_host_entry_point(cuda_lib):
     assert oracle.rel_err(tau, ref) <= TOL["float64"]
 
 
+def test_rnea_host_entry_point_pageable_and_fp32(cuda_lib):
+    """Pageable host arrays take the staged-copy path; pinned FP32 the in-place path."""
+    torch = _torch()
+    n, B = 16, 513
+    ch = chaingen.make_chain(n)
+    st = chaingen.make_states(B, n, seed=10)
+    model = cuda_lib.Model(ch)
+    for pin in (False, True):
+        args = [torch.from_numpy(st[k].astype(np.float32)) for k in ("q", "qd", "qdd")]
+        if pin:
+            args = [a.pin_memory() for a in args]
+        tau = cuda_lib.rnea_host(model, *args).numpy()
+        ref = oracle.rnea(ch, *(a.numpy().astype(np.float64) for a in args))
+        assert oracle.rel_err(tau, ref) <= TOL["float32"], pin
+
+
 def test_rnea_rejects_wrong_shapes(cuda_lib):
     torch = _torch()
     model = cuda_lib.Model(chaingen.make_chain(6))
