@@ -139,13 +139,12 @@ int rnea_batch(const rd_model *model, int B, int dtype, const void *q, const voi
 
 /*
  * rnea_batch_host -- rnea_batch on HOST arrays; returns when tau is on the host.
- * When all four arrays are pinned (page-locked or registered) host memory, the
- * kernel reads and writes them in place through their device-visible
- * addresses (no staging copies; the host link is coherent on Grace-Blackwell).
- * Otherwise q, qd, qdd are copied into device buffers owned by the model
- * (grown on demand: only this path may allocate device memory; rnea_batch
- * never does), the kernel runs, and tau is copied back. Same argument meaning
- * as rnea_batch.
+ * q, qd, qdd are copied into device buffers owned by the model (grown on
+ * demand: only this path may allocate device memory; rnea_batch never does),
+ * the kernel runs, and tau is copied back. Large batches are split into row
+ * chunks that alternate between the caller's stream and a side stream, so the
+ * copies of one chunk overlap the work of the next. Pinned host memory copies
+ * at full link speed. Same argument meaning as rnea_batch.
  */
 int rnea_batch_host(rd_model *model, int B, int dtype, const void *q, const void *qd,
                     const void *qdd, void *tau, const double *base, int variant,

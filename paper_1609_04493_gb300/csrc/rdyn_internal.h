@@ -22,6 +22,8 @@ struct rd_model {
     // device staging for the host-pointer entry points, grown on demand
     void *d_io = nullptr;
     size_t io_bytes = 0;
+    cudaStream_t io_side = nullptr;  // second stream of the host-array pipeline
+    cudaEvent_t io_fork = nullptr, io_join = nullptr;
     std::mutex io_mu;
 };
 

@@ -28,23 +28,6 @@ extern "C" int rnea_batch(const rd_model *m, int B, int dtype, const void *q, co
     return rd_rnea_dispatch_f64(m, B, q, qd, qdd, tau, b18, variant, s);
 }
 
-namespace {
-
-// Device-visible address of a pinned (page-locked or registered) host buffer,
-// or nullptr when the pointer is not one.
-const void *pinned_device_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
-    return a.devicePointer;
-}
-
-}  // namespace
-
 extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, const void *qd,
                                const void *qdd, void *tau, const double *base, int variant,
                                void *stream)
@@ -57,25 +40,13 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
     if (B == 0) return RD_OK;
     if (!q || !qd || !qdd || !tau)
         return rd_fail(RD_ERR_ARG, "rnea_batch_host: null batch pointer");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    // Pinned host arrays: the kernel reads and writes them in place over the
-    // host link (coherent on Grace-Blackwell), no staging copies.
-    const void *dq = pinned_device_ptr(q), *dqd = pinned_device_ptr(qd),
-               *dqdd = pinned_device_ptr(qdd), *dtau = pinned_device_ptr(tau);
-    if (dq && dqd && dqdd && dtau) {
-        int rc = rnea_batch(m, B, dtype, dq, dqd, dqdd, const_cast<void *>(dtau), base, variant,
-                            stream);
-        if (rc) return rc;
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: synchronize");
-        return RD_OK;
-    }
-    // Otherwise stage through device buffers owned by the model.
     const size_t esz = dtype == RD_F32 ? 4 : 8;
-    const size_t arr = (size_t)B * m->n * esz;
+    const size_t row = (size_t)m->n * esz;
+    const size_t arr = (size_t)B * row;
     const size_t slot = (arr + 255) & ~(size_t)255;
     std::lock_guard<std::mutex> lk(m->io_mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
     if (m->io_bytes < 4 * slot) {
         if (m->d_io) {
             e = cudaStreamSynchronize(s);
@@ -89,16 +60,38 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
                                              cudaGetErrorString(e));
         m->io_bytes = 4 * slot;
     }
+    if (!m->io_side) {
+        e = cudaStreamCreateWithFlags(&m->io_side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->io_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->io_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: stream set-up");
+    }
     char *d = static_cast<char *>(m->d_io);
-    void *sq = d, *sqd = d + slot, *sqdd = d + 2 * slot, *stau = d + 3 * slot;
-    e = cudaMemcpyAsync(sq, q, arr, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sqd, qd, arr, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sqdd, qdd, arr, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to device");
-    int rc = rnea_batch(m, B, dtype, sq, sqd, sqdd, stau, base, variant, stream);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(tau, stau, arr, cudaMemcpyDeviceToHost, s);
+    char *dq = d, *dqd = d + slot, *dqdd = d + 2 * slot, *dtau = d + 3 * slot;
+    // Row chunks alternate between the caller's stream and a side stream, so the
+    // copies of one chunk overlap the kernel and copies of the next.
+    const int chunks = B >= 4 * 8192 ? 4 : (B >= 2 * 8192 ? 2 : 1);
+    e = cudaEventRecord(m->io_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_side, m->io_fork, 0);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: fork");
+    for (int c = 0; c < chunks; ++c) {
+        const int b0 = (int)((long long)B * c / chunks), b1 = (int)((long long)B * (c + 1) / chunks);
+        const size_t o = (size_t)b0 * row, len = (size_t)(b1 - b0) * row;
+        cudaStream_t sc = (c & 1) ? m->io_side : s;
+        e = cudaMemcpyAsync(dq + o, static_cast<const char *>(q) + o, len, cudaMemcpyHostToDevice, sc);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dqd + o, static_cast<const char *>(qd) + o, len, cudaMemcpyHostToDevice, sc);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dqdd + o, static_cast<const char *>(qdd) + o, len, cudaMemcpyHostToDevice, sc);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to device");
+        int rc = rnea_batch(m, b1 - b0, dtype, dq + o, dqd + o, dqdd + o, dtau + o, base, variant, sc);
+        if (rc) return rc;
+        e = cudaMemcpyAsync(static_cast<char *>(tau) + o, dtau + o, len, cudaMemcpyDeviceToHost, sc);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to host");
+    }
+    e = cudaEventRecord(m->io_join, m->io_side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->io_join, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to host");
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: synchronize");
     return RD_OK;
 }
