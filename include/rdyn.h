@@ -241,6 +241,21 @@ int aba_batch(const rd_model *model, int B, int dtype, const void *q, const void
 /* Bytes of workspace aba_batch needs for B states with these flags. */
 int aba_workspace_size(const rd_model *model, int B, int dtype, int flags, size_t *bytes);
 
+/*
+ * jsiia_batch -- forward dynamics for B states by joint-space-inertia inversion
+ * (Sec. III-C, Eqs. tau-bias and JSIinv; Algorithm 2), for n <= 32: the n
+ * columns M_{.,j}(q) = ID(q, 0, delta_j, 0, 0, 0) and tau_bias = ID(q, qd, 0, ...)
+ * evaluated in parallel (one lane each), then a Cholesky solve of
+ * M qdd = tau - tau_bias. Columns and bias in dtype; factorisation and solve in
+ * FP64. One warp per instance; no workspace.
+ *   q, qd, tau  device, [B, n] inputs; qdd device [B, n] output.
+ *   status      device int[B] or NULL: RD_WARN_SINGULAR when a pivot is not
+ *               positive or qdd is not finite.
+ * Errors: RD_ERR_RANGE (n > 32 or B < 0), RD_ERR_ARG, RD_ERR_DTYPE, RD_ERR_CUDA.
+ */
+int jsiia_batch(const rd_model *model, int B, int dtype, const void *q, const void *qd,
+                const void *tau, void *qdd, const double *base, int *status, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Fleets: many chains of different lengths, mixed requests in one call.
  * ------------------------------------------------------------------------- */

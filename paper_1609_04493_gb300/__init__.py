@@ -25,6 +25,8 @@ from .binding import (  # noqa: F401
     rnea_host,
     rnea_vjp,
     aba,
+    jsiia,
+    forward_dynamics,
     aba_workspace_bytes,
     RD_ABA_SCANS_IN_DTYPE,
     rnea_autograd,
