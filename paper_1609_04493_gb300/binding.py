@@ -16,6 +16,7 @@ RD_VARIANT_AUTO = 0
 RD_VARIANT_SERIAL = 1
 RD_VARIANT_SERIAL_RECOMPUTE = 2
 RD_VARIANT_SERIAL_RECOMPUTE_CS = 3
+RD_VARIANT_SERIAL_REGSTATE = 4
 
 
 RD_FLAG_FAST_TRIG = 0x1000
@@ -30,6 +31,10 @@ def RD_VARIANT_SCAN(lanes):
 
 def RD_TUNE_BLOCK(threads):
     return {32: 5 << 16, 64: 6 << 16, 128: 7 << 16}.get(int(threads), 0)
+
+
+def RD_TUNE_REGLINKS(links):
+    return (int(links) // 4) << 20
 
 
 _ERRORS = {-1: "RD_ERR_ARG", -2: "RD_ERR_DTYPE", -3: "RD_ERR_RANGE", -4: "RD_ERR_CUDA",

@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "rdyn_internal.h"
+#include "rnea_regstate.cuh"
 #include "rnea_scan.cuh"
 #include "rnea_serial.cuh"
 
@@ -168,6 +169,57 @@ int launch_scan(const rd_model *m, int lanes, int B, const void *q, const void *
     }
 }
 
+template <typename T, int BLOCK, int RL>
+int launch_regstate_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                      void *tau, const double *base18, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    const int n = m->n;
+    const size_t smem = (size_t)n * kLinkConsts * sizeof(T) +
+                        (size_t)stage_bytes_per_thread<T>() * BLOCK +
+                        (size_t)(n > RL ? n - RL : 0) * state_bytes_per_link<T>(kStore) * BLOCK;
+    if (smem > (size_t)max_smem_optin(m->device))  // long chain: keep no per-link state
+        return launch_serial<T, 64, kRecompute>(m, B, q, qd, qdd, tau, base18, false, stream);
+    auto kern = rnea_regstate_kernel<T, BLOCK, RL>;
+    cudaError_t e = allow_smem(kern, m->device, configured);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+    const T *consts = nullptr;
+    if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
+    else consts = reinterpret_cast<const T *>(m->d_c64);
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    kern<<<grid, BLOCK, smem, stream>>>(consts, n, B, static_cast<const T *>(q),
+                                        static_cast<const T *>(qd), static_cast<const T *>(qdd),
+                                        static_cast<T *>(tau), make_base<T>(base18));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea regstate kernel launch");
+    return RD_OK;
+}
+
+// Register-plus-shared-memory state; needs whole 16-byte chunks (else the
+// shared-memory-state kernel runs instead).
+template <typename T>
+int launch_regstate(const rd_model *m, int block, int reglinks, int B, const void *q,
+                    const void *qd, const void *qdd, void *tau, const double *base18, bool fast,
+                    cudaStream_t s)
+{
+    const bool vec = (m->n % 4 == 0) && aligned16(q) && aligned16(qd) && aligned16(qdd) &&
+                     aligned16(tau);
+    if (!vec || fast)
+        return launch_mode<T, kStore>(m, block ? block : 32, B, q, qd, qdd, tau, base18, fast, s);
+    if (!block) block = 32;
+    if (!reglinks) reglinks = 16;
+#define RD_REGSTATE_CASE(BL, RLK)                                                   \
+    if (block == BL && reglinks == RLK)                                             \
+        return launch_regstate_k<T, BL, RLK>(m, B, q, qd, qdd, tau, base18, s);
+    RD_REGSTATE_CASE(32, 8)
+    RD_REGSTATE_CASE(32, 16)
+    RD_REGSTATE_CASE(64, 8)
+    RD_REGSTATE_CASE(64, 16)
+#undef RD_REGSTATE_CASE
+    return rd_fail(RD_ERR_ARG, "rnea_batch: register-state kernel not built for %d threads, "
+                               "%d register links", block, reglinks);
+}
+
 template <typename T>
 int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd, void *tau,
              const double *base18, int variant, cudaStream_t s)
@@ -175,8 +227,9 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     const int n = m->n;
     const size_t limit = (size_t)max_smem_optin(m->device);
     const bool fast = (variant & RD_FLAG_FAST_TRIG) != 0;
-    int block = (variant >> 16) & 0xff;
+    int block = (variant >> 16) & 0xf;
     if (block) block = 1 << block;
+    const int reglinks = 4 * ((variant >> 20) & 0xf);
     variant &= 0xfff;
     if (variant == RD_VARIANT_AUTO && B <= 152 * 32 && n <= 128) {
         // Fewer instances than one warp per SM: the serial recursion leaves the
@@ -201,6 +254,12 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
             variant = RD_VARIANT_SERIAL;
             if (!block) block = n > 16 ? 32 : 64;
         } else if (sizeof(T) == 8 && n <= 32) {
+            // FP64, 16 < n <= 32: the first 16 links' state in registers
+            // (812 us vs 934 us for cos/sin-only state at n = 32)
+            if (n % 4 == 0) {
+                return launch_regstate<T>(m, block ? block : 32, reglinks ? reglinks : 16, B, q,
+                                          qd, qdd, tau, base18, fast, s);
+            }
             variant = RD_VARIANT_SERIAL_RECOMPUTE_CS;
             if (!block) block = 32;
         } else {
@@ -217,6 +276,8 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         }
         return launch_mode<T, kStore>(m, block, B, q, qd, qdd, tau, base18, fast, s);
     }
+    if (variant == RD_VARIANT_SERIAL_REGSTATE)
+        return launch_regstate<T>(m, block, reglinks, B, q, qd, qdd, tau, base18, fast, s);
     if (!block) block = 64;
     if (variant == RD_VARIANT_SERIAL_RECOMPUTE)
         return launch_mode<T, kRecompute>(m, block, B, q, qd, qdd, tau, base18, fast, s);

@@ -217,3 +217,15 @@ def test_rnea_scan_rejects_too_many_links(cuda_lib):
     x = torch.zeros((4, 20), device="cuda")
     with pytest.raises(cuda_lib.RdError):
         cuda_lib.rnea(model, x, x, x, variant=cuda_lib.RD_VARIANT_SCAN(2))
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("reglinks,block", [(8, 32), (16, 32), (8, 64), (16, 64)])
+@pytest.mark.parametrize("n", [4, 8, 12, 16, 20, 32, 64, 100])
+def test_rnea_register_state_parity(cuda_lib, n, reglinks, block, dtype):
+    """Register-plus-shared-memory state kernel, with chains shorter and longer
+    than the register part."""
+    v = cuda_lib.RD_VARIANT_SERIAL_REGSTATE | cuda_lib.RD_TUNE_REGLINKS(reglinks) | \
+        cuda_lib.RD_TUNE_BLOCK(block)
+    tau, ref = run_case(cuda_lib, n, 333, dtype, v, seed=17)
+    assert oracle.rel_err(tau, ref) <= TOL[dtype]
