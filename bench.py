@@ -37,7 +37,12 @@ METRIC = "RNEA evals/s at n=32,B=65536 FP32 vs FP64; adjoint evals/s; % of roofl
 UNIT = "evals/s"
 WORKLOAD = "rnea_n32_B65536"
 ROTATE = 8  # input sets cycled between steps; 8 x 33.5 MB > 2 x L2 (129 MB)
-FLOP_PER_LINK = 280     # FP32/FP64 arithmetic of the joint-frame formulation, FMA = 2
+FLOP_PER_LINK = 274     # arithmetic of the joint-frame formulation per link, FMA = 2:
+                        # rotation 18 + forward step 94 + bias wrench 102 + carry 60
+# adjoint arithmetic per link (FMA = 2): sweep 1 155 (rotation, motion, wrench
+# adjoint), sweep 2 500 (bias wrench, carries, inertia products, ad terms,
+# gradients) plus 137 to re-derive the motion and wrench adjoint (recompute mode)
+VJP_FLOP_PER_LINK = {1: 655, 2: 792}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
@@ -264,8 +269,12 @@ def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
 
         t = time_calls(torch, call, steps, 3, dist, sampler)
         name = f"B{B}_{'store' if mode == rd.RD_VJP_STORE else 'recompute'}"
+        fpl = VJP_FLOP_PER_LINK[mode]
+        tf = B * N_LINKS * fpl / (t / steps) / 1e12
+        peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
         out[name] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
-                     "steps": steps}
+                     "steps": steps, "flop_per_link": fpl, "achieved_tflops": tf,
+                     "frac_of_fp32_peak": tf / peak32}
     out["metric"] = "RNEA adjoint d(w^T tau)/d(q, qd, qdd) evals/s, n=32 FP32"
     return out
 
