@@ -69,9 +69,13 @@ enum rd_variant {
     RD_VARIANT_SERIAL_RECOMPUTE = 2, /* one thread per instance, backward sweep re-derives
                                         V_{i-1}, dV_{i-1} from V_i, dV_i; no per-link state */
     RD_VARIANT_SERIAL_RECOMPUTE_CS = 3, /* as 2, keeping cos/sin of q_i in shared memory */
-    RD_VARIANT_SERIAL_REGSTATE = 4 /* as 1, the state of the first links (RD_TUNE_REGLINKS,
-                                      default 16) held in registers, the rest in shared memory;
-                                      needs n % 4 == 0 and 16-byte aligned rows */
+    RD_VARIANT_SERIAL_REGSTATE = 4, /* as 1, the state of the first links (RD_TUNE_REGLINKS,
+                                       default 16) held in registers, the rest in shared memory;
+                                       needs n % 4 == 0 and 16-byte aligned rows */
+    RD_VARIANT_SERIAL_HYBRID = 5 /* one thread per instance, per-link state in shared memory
+                                    for the first K links only (RD_TUNE_STORED_LINKS(K), K a
+                                    multiple of 4; 0 = library default); the backward sweep
+                                    re-derives the motion of links K..n-1 as variant 2 does */
 };
 /* Lane-parallel scan: L lanes of one warp per instance, L in {2,4,8,16,32};
  * each lane owns ceil(n/L) consecutive links, lanes combine their segments
@@ -89,6 +93,9 @@ enum rd_variant {
 /* OR-able tuning field for RD_VARIANT_SERIAL_REGSTATE: links whose state stays in
  * registers (8 or 16; 0 = library default). */
 #define RD_TUNE_REGLINKS(links) (((links) / 4) << 20)
+/* OR-able tuning field for RD_VARIANT_SERIAL_HYBRID: links whose state is kept
+ * (a multiple of 4, at most RD_MAX_LINKS; 0 = library default). */
+#define RD_TUNE_STORED_LINKS(links) (((links) / 4) << 20)
 
 #define RD_MAX_LINKS 128
 

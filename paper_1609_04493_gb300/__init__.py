@@ -16,7 +16,9 @@ from .binding import (  # noqa: F401
     RD_VARIANT_SERIAL_RECOMPUTE_CS,
     RD_TUNE_BLOCK,
     RD_TUNE_REGLINKS,
+    RD_TUNE_STORED_LINKS,
     RD_VARIANT_SERIAL_REGSTATE,
+    RD_VARIANT_SERIAL_HYBRID,
     RD_VARIANT_SCAN,
     RD_FLAG_FAST_TRIG,
     RdError,

@@ -3,8 +3,8 @@
 The paper names "an automatic scheduler for hardware-specific optimal
 performance" as future work (Sec. VI). Here the library exposes its choices as
 explicit variant codes (rnea_batch: per-thread serial recursion with one of
-three backward-state modes and a block size, or the lane-parallel scan with L
-lanes; fleet_batch: persistent CTA shape or one launch per group), and this
+four backward-state modes -- stored, stateless, cos/sin only, or stored for the
+first K links -- and a block size, or the lane-parallel scan with L lanes; fleet_batch: persistent CTA shape or one launch per group), and this
 module times the candidates on the caller's own data with CUDA events, keeps
 the fastest, and caches the answer in a JSON file keyed by GPU name, SM count
 and the workload's shape (RDYN_TUNE_CACHE, default ~/.cache/rdyn/tune.json).
@@ -74,6 +74,11 @@ def rnea_candidates(n, B, dtype):
         for mode in (b.RD_VARIANT_SERIAL, b.RD_VARIANT_SERIAL_RECOMPUTE,
                      b.RD_VARIANT_SERIAL_RECOMPUTE_CS):
             c.append(mode | b.RD_TUNE_BLOCK(block))
+    for block in (32, 64):  # state for the first K links only
+        for K in (4, 8, 12, 16, 24):
+            if K < n:
+                c.append(b.RD_VARIANT_SERIAL_HYBRID | b.RD_TUNE_STORED_LINKS(K) |
+                         b.RD_TUNE_BLOCK(block))
     for lanes in (2, 4, 8, 16, 32):
         if n <= 8 * lanes:
             c.append(b.RD_VARIANT_SCAN(lanes))

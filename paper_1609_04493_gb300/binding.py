@@ -17,6 +17,7 @@ RD_VARIANT_SERIAL = 1
 RD_VARIANT_SERIAL_RECOMPUTE = 2
 RD_VARIANT_SERIAL_RECOMPUTE_CS = 3
 RD_VARIANT_SERIAL_REGSTATE = 4
+RD_VARIANT_SERIAL_HYBRID = 5
 
 
 RD_FLAG_FAST_TRIG = 0x1000
@@ -34,6 +35,10 @@ def RD_TUNE_BLOCK(threads):
 
 
 def RD_TUNE_REGLINKS(links):
+    return (int(links) // 4) << 20
+
+
+def RD_TUNE_STORED_LINKS(links):
     return (int(links) // 4) << 20
 
 

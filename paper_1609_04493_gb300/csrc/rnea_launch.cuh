@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "rdyn_internal.h"
+#include "rnea_hybrid.cuh"
 #include "rnea_regstate.cuh"
 #include "rnea_scan.cuh"
 #include "rnea_serial.cuh"
@@ -115,6 +116,64 @@ int launch_mode(const rd_model *m, int block, int B, const void *q, const void *
     case 32: return launch_serial<T, 32, MODE>(m, B, q, qd, qdd, tau, base18, fast, s);
     case 64: return launch_serial<T, 64, MODE>(m, B, q, qd, qdd, tau, base18, fast, s);
     case 128: return launch_serial<T, 128, MODE>(m, B, q, qd, qdd, tau, base18, fast, s);
+    default: return rd_fail(RD_ERR_ARG, "rnea_batch: block size %d not built (32, 64, 128)", block);
+    }
+}
+
+template <typename T, int BLOCK, bool VEC, bool FAST>
+int launch_hybrid_k(const rd_model *m, int K, int B, const void *q, const void *qd,
+                    const void *qdd, void *tau, const double *base18, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    const int n = m->n;
+    const size_t smem = hybrid_smem_bytes<T>(n, K, BLOCK, VEC);
+    auto kern = rnea_hybrid_kernel<T, BLOCK, VEC, FAST>;
+    cudaError_t e = allow_smem(kern, m->device, configured);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+    const T *consts = nullptr;
+    if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
+    else consts = reinterpret_cast<const T *>(m->d_c64);
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    kern<<<grid, BLOCK, smem, stream>>>(consts, n, K, B, static_cast<const T *>(q),
+                                        static_cast<const T *>(qd), static_cast<const T *>(qdd),
+                                        static_cast<T *>(tau), make_base<T>(base18));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea hybrid kernel launch");
+    return RD_OK;
+}
+
+template <typename T, int BLOCK>
+int launch_hybrid_b(const rd_model *m, int K, int B, const void *q, const void *qd,
+                    const void *qdd, void *tau, const double *base18, bool fast, cudaStream_t s)
+{
+    const size_t limit = (size_t)max_smem_optin(m->device);
+    const bool vec = (m->n % 4 == 0) && aligned16(q) && aligned16(qd) && aligned16(qdd) &&
+                     aligned16(tau) && hybrid_smem_bytes<T>(m->n, K, BLOCK, true) <= limit;
+    if (!vec && hybrid_smem_bytes<T>(m->n, K, BLOCK, false) > limit)
+        return rd_fail(RD_ERR_ARG, "rnea_batch: state of %d links needs %zu bytes of shared "
+                                   "memory, %zu available", K,
+                       hybrid_smem_bytes<T>(m->n, K, BLOCK, false), limit);
+    if constexpr (sizeof(T) == 4) {
+        if (fast)
+            return vec ? launch_hybrid_k<T, BLOCK, true, true>(m, K, B, q, qd, qdd, tau, base18, s)
+                       : launch_hybrid_k<T, BLOCK, false, true>(m, K, B, q, qd, qdd, tau, base18, s);
+    }
+    return vec ? launch_hybrid_k<T, BLOCK, true, false>(m, K, B, q, qd, qdd, tau, base18, s)
+               : launch_hybrid_k<T, BLOCK, false, false>(m, K, B, q, qd, qdd, tau, base18, s);
+}
+
+// Stored-state prefix of K links (rounded up to whole chunks and capped at the
+// chain); the rest of the chain is recomputed in the backward sweep.
+template <typename T>
+int launch_hybrid(const rd_model *m, int block, int K, int B, const void *q, const void *qd,
+                  const void *qdd, void *tau, const double *base18, bool fast, cudaStream_t s)
+{
+    const int cap = 4 * ((m->n + 3) / 4);
+    K = K > cap ? cap : 4 * ((K + 3) / 4);
+    switch (block) {
+    case 32: return launch_hybrid_b<T, 32>(m, K, B, q, qd, qdd, tau, base18, fast, s);
+    case 64: return launch_hybrid_b<T, 64>(m, K, B, q, qd, qdd, tau, base18, fast, s);
+    case 128: return launch_hybrid_b<T, 128>(m, K, B, q, qd, qdd, tau, base18, fast, s);
     default: return rd_fail(RD_ERR_ARG, "rnea_batch: block size %d not built (32, 64, 128)", block);
     }
 }
@@ -229,7 +288,7 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     const bool fast = (variant & RD_FLAG_FAST_TRIG) != 0;
     int block = (variant >> 16) & 0xf;
     if (block) block = 1 << block;
-    const int reglinks = 4 * ((variant >> 20) & 0xf);
+    const int reglinks = 4 * ((variant >> 20) & 0xff);  // RD_TUNE_REGLINKS / _STORED_LINKS
     variant &= 0xfff;
     if (variant == RD_VARIANT_AUTO && B <= 152 * 32 && n <= 128) {
         // Fewer instances than one warp per SM: the serial recursion leaves the
@@ -246,13 +305,21 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         return launch_scan<T, false>(m, lanes, B, q, qd, qdd, tau, base18, s);
     }
     if (variant == RD_VARIANT_AUTO) {
-        // Sweep on GB300 at B = 65536 (modes x block sizes): per-link state in
-        // shared memory wins while it is small (FP32 n <= 32, FP64 n <= 16);
-        // FP64 up to n = 32 keeps only cos/sin; longer chains re-derive the
-        // motion in the backward sweep.
+        // Sweep on GB300 at B = 65536 (modes x block sizes x stored links):
+        // per-link state in shared memory wins while it is small (FP32 n <= 32,
+        // FP64 n <= 16); FP64 up to n = 32 keeps part of it in registers; up to
+        // n = 64 the first links keep their state and the rest are re-derived;
+        // longer chains re-derive the motion of every link in the backward sweep.
         if (n <= (sizeof(T) == 4 ? 32 : 16) && serial_smem<T>(n, 32, kStore, true) <= limit / 4) {
             variant = RD_VARIANT_SERIAL;
-            if (!block) block = n > 16 ? 32 : 64;
+            // FP64 n = 16: 393 us with 32 threads vs 408 with 64
+            if (!block) block = (sizeof(T) == 8 || n > 16) ? 32 : 64;
+        } else if (n <= 64 && (sizeof(T) == 4 || n > 32)) {
+            // 32 < n <= 64: state for the first links only. FP64 n = 48: 1492 us
+            // with 12 stored links vs 1719 stateless; n = 64: 2068 vs 2143 with 8;
+            // FP32 n = 48 / 64: 45.8 / 60.6 us with 8 vs 47.3 / 61.8.
+            const int K = reglinks ? reglinks : (sizeof(T) == 8 && n <= 48 ? 12 : 8);
+            return launch_hybrid<T>(m, block ? block : 64, K, B, q, qd, qdd, tau, base18, fast, s);
         } else if (sizeof(T) == 8 && n <= 32) {
             // FP64, 16 < n <= 32: the first 16 links' state in registers
             // (812 us vs 934 us for cos/sin-only state at n = 32)
@@ -278,6 +345,11 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     }
     if (variant == RD_VARIANT_SERIAL_REGSTATE)
         return launch_regstate<T>(m, block, reglinks, B, q, qd, qdd, tau, base18, fast, s);
+    if (variant == RD_VARIANT_SERIAL_HYBRID) {
+        if (!block) block = 32;
+        const int K = reglinks ? reglinks : 16;
+        return launch_hybrid<T>(m, block, K, B, q, qd, qdd, tau, base18, fast, s);
+    }
     if (!block) block = 64;
     if (variant == RD_VARIANT_SERIAL_RECOMPUTE)
         return launch_mode<T, kRecompute>(m, block, B, q, qd, qdd, tau, base18, fast, s);

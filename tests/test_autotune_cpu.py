@@ -21,3 +21,17 @@ def test_fleet_candidates_fit_a_cta():
     for sched, tune in autotune.fleet_candidates():
         if sched == b.RD_SCHED_PERSISTENT:
             assert (1 << (tune >> 8)) * (tune & 0xff) <= 1024
+
+
+def test_rnea_candidates_hybrid_store_fewer_links_than_the_chain():
+    """Partial-state candidates keep state for fewer links than the chain has
+    (K >= n is the stored kernel, already a candidate) and encode K / 4 in
+    bits 20..27."""
+    for n in (6, 16, 32, 100):
+        hy = [v for v in autotune.rnea_candidates(n, 65536, None)
+              if (v & 0xfff) == b.RD_VARIANT_SERIAL_HYBRID]
+        assert hy, n
+        for v in hy:
+            K = 4 * ((v >> 20) & 0xff)
+            assert 0 < K < n
+            assert ((v >> 16) & 0xf) in (5, 6)  # 32 or 64 threads

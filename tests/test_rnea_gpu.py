@@ -39,8 +39,8 @@ def run_case(rd, n, B, dtype, variant, seed=5, base=None, chain=None):
 
 
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
-@pytest.mark.parametrize("variant", ["serial", "recompute"])
-@pytest.mark.parametrize("n", [1, 2, 7, 16, 31, 32, 33, 64, 100, 128])
+@pytest.mark.parametrize("variant", ["auto", "serial", "recompute"])
+@pytest.mark.parametrize("n", [1, 2, 7, 16, 31, 32, 33, 48, 64, 100, 128])
 def test_rnea_parity(cuda_lib, n, dtype, variant):
     B = 1000  # several blocks and a ragged tail
     if variant == "serial" and dtype == "float64" and n > 100:
