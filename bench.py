@@ -450,8 +450,8 @@ def run_ours(args):
         res["e2e"] = {"value": world * BATCH * Ke / te, "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
                       "d2h_bytes_per_step": BATCH * N_LINKS * 4,
-                      "api": "rnea_batch_host, pinned host arrays, FP32 (copies pipelined "
-                             "in 4 row chunks over two streams)"}
+                      "api": "rnea_batch_host, pinned host arrays, FP32 (row chunks "
+                             "pipelined: copies in, kernel, copies out on three streams)"}
 
         # ---- adjoint (rnea_vjp), n = 32 FP32
         res["adjoint"] = adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K)

@@ -251,8 +251,9 @@ def rnea_host(model, q, qd, qdd, out=None, base=None, variant=RD_VARIANT_AUTO, s
             raise ValueError("rnea_host expects contiguous host arrays of one shape and dtype")
     if arrs[0].dim() != 2 or arrs[0].shape[1] != model.n:
         raise ValueError(f"expected shape [B, {model.n}]")
-    if out is None:
-        out = torch.empty_like(arrs[0])
+    if out is None:  # pinned when the inputs are, so the recorded pipeline can serve it
+        out = torch.empty(arrs[0].shape, dtype=arrs[0].dtype,
+                          pin_memory=bool(arrs[0].is_pinned()))
     if stream is None:
         stream = torch.cuda.current_stream()
     keep, bp = _base_arg(base)

@@ -22,8 +22,10 @@ struct rd_model {
     // device staging for the host-pointer entry points, grown on demand
     void *d_io = nullptr;
     size_t io_bytes = 0;
-    cudaStream_t io_side = nullptr;  // second stream of the host-array pipeline
-    cudaEvent_t io_fork = nullptr, io_join = nullptr;
+    // host-array pipeline: copies in on io_in, kernels on the caller's stream,
+    // copies out on io_out, chained per chunk by io_in_done / io_kern_done
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    cudaEvent_t io_fork = nullptr, io_join = nullptr, io_in_done = nullptr, io_kern_done = nullptr;
     std::mutex io_mu;
 };
 

@@ -255,9 +255,12 @@ extern "C" void rd_model_destroy(rd_model *m)
     if (m->d_c32) cudaFree(m->d_c32);
     if (m->d_c64) cudaFree(m->d_c64);
     if (m->d_io) cudaFree(m->d_io);
-    if (m->io_side) cudaStreamDestroy(m->io_side);
+    if (m->io_in) cudaStreamDestroy(m->io_in);
+    if (m->io_out) cudaStreamDestroy(m->io_out);
     if (m->io_fork) cudaEventDestroy(m->io_fork);
     if (m->io_join) cudaEventDestroy(m->io_join);
+    if (m->io_in_done) cudaEventDestroy(m->io_in_done);
+    if (m->io_kern_done) cudaEventDestroy(m->io_kern_done);
     if (prev >= 0 && prev != m->device) cudaSetDevice(prev);
     delete m;
 }

@@ -28,6 +28,63 @@ extern "C" int rnea_batch(const rd_model *m, int B, int dtype, const void *q, co
     return rd_rnea_dispatch_f64(m, B, q, qd, qdd, tau, b18, variant, s);
 }
 
+// Rows per chunk of the host-array pipeline (B = 65536, n = 32 in FP32: 212 us
+// per call with two chunks of 32768 rows, 223 with 16384, 248 with 8192: every
+// chunk adds host-side calls and a copy start-up that outweigh the overlap).
+#ifndef RD_HOST_CHUNK_ROWS
+#define RD_HOST_CHUNK_ROWS 32768
+#endif
+constexpr int kHostMaxChunks = 16;
+
+namespace {
+
+// Three-stage pipeline over row chunks on (io_in, s, io_out): the inputs of
+// chunk c+1 stream in while chunk c is computed and chunk c-1 streams out, so
+// the inbound copies run back to back. A stream-wait captures the event as last
+// recorded, so one pair of events serves every chunk. Enqueues only.
+int enqueue_host_pipeline(rd_model *m, int B, int dtype, const void *q, const void *qd,
+                          const void *qdd, void *tau, const double *base, int variant,
+                          cudaStream_t s, size_t slot)
+{
+    const size_t row = (size_t)m->n * (dtype == RD_F32 ? 4 : 8);
+    char *d = static_cast<char *>(m->d_io);
+    char *dq = d, *dqd = d + slot, *dqdd = d + 2 * slot, *dtau = d + 3 * slot;
+    // whole chunks of at least RD_HOST_CHUNK_ROWS rows (above the batch size
+    // below which AUTO picks the lane-parallel scan), so the kernel chosen per
+    // chunk, and with it the rounding, is the one the whole batch would get
+    const long long nch = (long long)B / RD_HOST_CHUNK_ROWS;
+    const int chunks = nch < 1 ? 1 : (nch > kHostMaxChunks ? kHostMaxChunks : (int)nch);
+    cudaError_t e = cudaEventRecord(m->io_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_in, m->io_fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_out, m->io_fork, 0);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: fork");
+    for (int c = 0; c < chunks; ++c) {
+        const int b0 = (int)((long long)B * c / chunks), b1 = (int)((long long)B * (c + 1) / chunks);
+        const size_t o = (size_t)b0 * row, len = (size_t)(b1 - b0) * row;
+        e = cudaMemcpyAsync(dq + o, static_cast<const char *>(q) + o, len, cudaMemcpyHostToDevice, m->io_in);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dqd + o, static_cast<const char *>(qd) + o, len, cudaMemcpyHostToDevice, m->io_in);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dqdd + o, static_cast<const char *>(qdd) + o, len, cudaMemcpyHostToDevice, m->io_in);
+        if (e == cudaSuccess) e = cudaEventRecord(m->io_in_done, m->io_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->io_in_done, 0);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to device");
+        int rc = rnea_batch(m, b1 - b0, dtype, dq + o, dqd + o, dqdd + o, dtau + o, base, variant, s);
+        if (rc) return rc;
+        e = cudaEventRecord(m->io_kern_done, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_out, m->io_kern_done, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<char *>(tau) + o, dtau + o, len, cudaMemcpyDeviceToHost, m->io_out);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to host");
+    }
+    e = cudaEventRecord(m->io_join, m->io_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->io_join, 0);
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: join");
+    return RD_OK;
+}
+
+}  // namespace
+
 extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, const void *qd,
                                const void *qdd, void *tau, const double *base, int variant,
                                void *stream)
@@ -41,8 +98,7 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
     if (!q || !qd || !qdd || !tau)
         return rd_fail(RD_ERR_ARG, "rnea_batch_host: null batch pointer");
     const size_t esz = dtype == RD_F32 ? 4 : 8;
-    const size_t row = (size_t)m->n * esz;
-    const size_t arr = (size_t)B * row;
+    const size_t arr = (size_t)B * (size_t)m->n * esz;
     const size_t slot = (arr + 255) & ~(size_t)255;
     std::lock_guard<std::mutex> lk(m->io_mu);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -60,38 +116,17 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
                                              cudaGetErrorString(e));
         m->io_bytes = 4 * slot;
     }
-    if (!m->io_side) {
-        e = cudaStreamCreateWithFlags(&m->io_side, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->io_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->io_join, cudaEventDisableTiming);
+    if (!m->io_in) {
+        e = cudaStreamCreateWithFlags(&m->io_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->io_out, cudaStreamNonBlocking);
+        cudaEvent_t *evs[4] = {&m->io_fork, &m->io_join, &m->io_in_done, &m->io_kern_done};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
         if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: stream set-up");
     }
-    char *d = static_cast<char *>(m->d_io);
-    char *dq = d, *dqd = d + slot, *dqdd = d + 2 * slot, *dtau = d + 3 * slot;
-    // Row chunks alternate between the caller's stream and a side stream, so the
-    // copies of one chunk overlap the kernel and copies of the next.
-    const int chunks = B >= 4 * 8192 ? 4 : (B >= 2 * 8192 ? 2 : 1);
-    e = cudaEventRecord(m->io_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->io_side, m->io_fork, 0);
-    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: fork");
-    for (int c = 0; c < chunks; ++c) {
-        const int b0 = (int)((long long)B * c / chunks), b1 = (int)((long long)B * (c + 1) / chunks);
-        const size_t o = (size_t)b0 * row, len = (size_t)(b1 - b0) * row;
-        cudaStream_t sc = (c & 1) ? m->io_side : s;
-        e = cudaMemcpyAsync(dq + o, static_cast<const char *>(q) + o, len, cudaMemcpyHostToDevice, sc);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dqd + o, static_cast<const char *>(qd) + o, len, cudaMemcpyHostToDevice, sc);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dqdd + o, static_cast<const char *>(qdd) + o, len, cudaMemcpyHostToDevice, sc);
-        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to device");
-        int rc = rnea_batch(m, b1 - b0, dtype, dq + o, dqd + o, dqdd + o, dtau + o, base, variant, sc);
-        if (rc) return rc;
-        e = cudaMemcpyAsync(static_cast<char *>(tau) + o, dtau + o, len, cudaMemcpyDeviceToHost, sc);
-        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: copy to host");
-    }
-    e = cudaEventRecord(m->io_join, m->io_side);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->io_join, 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = enqueue_host_pipeline(m, B, dtype, q, qd, qdd, tau, base, variant, s, slot);
+    if (rc) return rc;
+    e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: synchronize");
     return RD_OK;
 }

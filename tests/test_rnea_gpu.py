@@ -170,6 +170,51 @@ def test_rnea_host_entry_point_pageable_and_fp32(cuda_lib):
         assert oracle.rel_err(tau, ref) <= TOL["float32"], pin
 
 
+@pytest.mark.parametrize("B", [8192 * 3 + 77, 300001])
+def test_rnea_host_pipeline_chunks(cuda_lib, B):
+    """Host arrays spanning several pipeline chunks (ragged last chunk; more rows
+    than the chunk cap, so chunks grow): every instance against the device-array
+    entry point, which is itself checked against the oracle elsewhere, and a
+    sample against the oracle."""
+    torch = _torch()
+    n = 7
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    st = chaingen.make_states(B, n, seed=12)
+    model = cuda_lib.Model(ch)
+    args = [torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("q", "qd", "qdd")]
+    tau = cuda_lib.rnea_host(model, *args).numpy()
+    dev = cuda_lib.rnea(model, *(a.cuda() for a in args)).cpu().numpy()
+    assert np.array_equal(tau, dev)
+    idx = np.arange(0, B, 97)
+    ref = oracle.rnea(ch, *(a.numpy()[idx].astype(np.float64) for a in args))
+    assert oracle.rel_err(tau[idx].astype(np.float64), ref) <= TOL["float32"]
+
+
+def test_rnea_host_repeated_calls_use_current_data(cuda_lib):
+    """Repeated calls with the same pinned buffers (the device staging buffers are
+    reused): new contents in the same buffers, a new boundary state and a new
+    batch size all give the fresh result, identical to the device path."""
+    torch = _torch()
+    n, B = 8, 3 * 8192 + 5
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    model = cuda_lib.Model(ch)
+    bufs = [torch.empty((B, n), dtype=torch.float32).pin_memory() for _ in range(3)]
+    out = torch.empty((B, n), dtype=torch.float32).pin_memory()
+    base2 = np.array([0, 0, 0, 0, 0, 0, 0, 0, 9.81, 0, 0, 0, 1.0, 0.5, -0.5, 0.1, 0.2, 0.3])
+    for step, (seed, base, rows) in enumerate([(1, None, B), (1, None, B), (2, None, B),
+                                               (3, base2, B), (3, base2, B), (4, None, B - 8192)]):
+        st = chaingen.make_states(B, n, seed=seed)
+        for bf, k in zip(bufs, ("q", "qd", "qdd")):
+            bf.copy_(torch.from_numpy(st[k].astype(np.float32)))
+        args = [bf[:rows] for bf in bufs]
+        tau = cuda_lib.rnea_host(model, *args, out=out[:rows], base=base).numpy().copy()
+        dev = cuda_lib.rnea(model, *(a.cuda() for a in args), base=base).cpu().numpy()
+        assert np.array_equal(tau, dev), step
+        idx = np.arange(0, rows, 211)
+        ref = oracle.rnea(ch, *(a.numpy()[idx].astype(np.float64) for a in args), base=base)
+        assert oracle.rel_err(tau[idx].astype(np.float64), ref) <= TOL["float32"], step
+
+
 def test_rnea_rejects_wrong_shapes(cuda_lib):
     torch = _torch()
     model = cuda_lib.Model(chaingen.make_chain(6))
