@@ -72,19 +72,32 @@ enum rd_variant {
     RD_VARIANT_SERIAL_REGSTATE = 4, /* as 1, the state of the first links (RD_TUNE_REGLINKS,
                                        default 16) held in registers, the rest in shared memory;
                                        needs n % 4 == 0 and 16-byte aligned rows */
-    RD_VARIANT_SERIAL_HYBRID = 5 /* one thread per instance, per-link state in shared memory
+    RD_VARIANT_SERIAL_HYBRID = 5, /* one thread per instance, per-link state in shared memory
                                     for the first K links only (RD_TUNE_STORED_LINKS(K), K a
                                     multiple of 4; 0 = library default); the backward sweep
                                     re-derives the motion of links K..n-1 as variant 2 does */
+    RD_VARIANT_SERIAL_DH = 6, /* one thread per instance in common-normal link frames: each
+                                 link transform is Rx(alpha_i) Rz(theta0_i + q_i) plus an offset
+                                 (the Denavit-Hartenberg structure), built once by
+                                 rd_model_create. With n % 4 == 0, n <= 128 and 16-byte aligned
+                                 rows the link constants travel as a kernel parameter and the
+                                 full backward-sweep state is kept for the first K links
+                                 (RD_TUNE_STORED_LINKS(K); 0 = library default), cos/sin only
+                                 for the rest, whose motion is re-derived; otherwise every link
+                                 keeps its state in shared memory. AUTO takes this kernel for
+                                 FP32 batches of more than 2048 whole-chunk rows. */
+    RD_VARIANT_SERIAL_DH_RECOMPUTE = 7 /* as 6 with K = 0 (no full state) */
 };
 /* Lane-parallel scan: L lanes of one warp per instance, L in {2,4,8,16,32};
  * each lane owns ceil(n/L) consecutive links, lanes combine their segments
  * with warp-shuffle log-step semigroup scans (Sec. III). */
 #define RD_VARIANT_SCAN(L) (0x100 | (L))
 /* OR-able flag: in FP32, evaluate sin/cos of q_i by a 2*pi range reduction
- * plus the hardware approximation (absolute error ~4e-7) instead of the
- * default accurate library routine. Faster; the torque error can then exceed
- * 1e-4 of max|tau| on instances whose torques nearly cancel. */
+ * plus the special-function-unit approximation (absolute error ~4e-7) instead
+ * of the default: the library routine in the joint-frame kernels, an FMA-pipe
+ * polynomial (absolute error < 1.2e-7, see rd_joint_trig) in the
+ * common-normal-frame kernels. Faster; the torque error can then exceed 1e-4
+ * of max|tau| on instances whose torques nearly cancel. */
 #define RD_FLAG_FAST_TRIG 0x1000
 /* OR-able tuning field: threads per block of the one-thread-per-instance
  * kernels (32, 64 or 128; 0 = library default). */
@@ -344,6 +357,17 @@ int fleet_batch(const rd_plan *plan, const void *q, const void *qd, const void *
  * Allocates a small device buffer and synchronizes the stream.
  */
 int rd_measure_fma_peak(int dtype, double *tflops, void *stream);
+
+/*
+ * rd_joint_trig -- diagnostic, outside the paper's method: the FP32 sine and
+ * cosine that the common-normal-frame kernels evaluate for each joint angle
+ * (Cody-Waite reduction by pi/2 and fitted polynomials on the FMA pipe; with
+ * flags & RD_FLAG_FAST_TRIG, the special-function-unit approximation).
+ *   x, s, c  device float[count]: angles in radians in, sin and cos out.
+ *   stream   cudaStream_t. Asynchronous; never allocates.
+ * Errors: RD_ERR_RANGE (count < 0), RD_ERR_ARG (null pointer), RD_ERR_CUDA.
+ */
+int rd_joint_trig(int flags, const float *x, float *s, float *c, int count, void *stream);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *rd_last_error(void);

@@ -19,6 +19,8 @@ from .binding import (  # noqa: F401
     RD_TUNE_STORED_LINKS,
     RD_VARIANT_SERIAL_REGSTATE,
     RD_VARIANT_SERIAL_HYBRID,
+    RD_VARIANT_SERIAL_DH,
+    RD_VARIANT_SERIAL_DH_RECOMPUTE,
     RD_VARIANT_SCAN,
     RD_FLAG_FAST_TRIG,
     RdError,
@@ -40,6 +42,7 @@ from .binding import (  # noqa: F401
     RD_VJP_RECOMPUTE,
     default_base,
     measure_fma_peak,
+    joint_trig,
     Fleet,
     Plan,
     fleet_batch,

@@ -18,6 +18,8 @@ RD_VARIANT_SERIAL_RECOMPUTE = 2
 RD_VARIANT_SERIAL_RECOMPUTE_CS = 3
 RD_VARIANT_SERIAL_REGSTATE = 4
 RD_VARIANT_SERIAL_HYBRID = 5
+RD_VARIANT_SERIAL_DH = 6
+RD_VARIANT_SERIAL_DH_RECOMPUTE = 7
 
 
 RD_FLAG_FAST_TRIG = 0x1000
@@ -117,6 +119,8 @@ def load(build_if_missing=True):
         lib.jsiia_batch.restype = I
         lib.rd_measure_fma_peak.argtypes = [I, D, P]
         lib.rd_measure_fma_peak.restype = I
+        lib.rd_joint_trig.argtypes = [I, P, P, P, I, P]
+        lib.rd_joint_trig.restype = I
         _lib = lib
         return lib
 
@@ -140,6 +144,21 @@ def measure_fma_peak(dtype="float32", stream=None):
     _check(lib.rd_measure_fma_peak(RD_F32 if dtype == "float32" else RD_F64, ctypes.byref(out),
                                    ctypes.c_void_p(st.cuda_stream)))
     return out.value
+
+
+def joint_trig(x, fast=False, stream=None):
+    """(sin x, cos x) as the FP32 common-normal-frame kernels evaluate them
+    (rd_joint_trig; diagnostic). x: contiguous float32 CUDA tensor."""
+    import torch
+
+    lib = load()
+    if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("joint_trig expects a contiguous float32 CUDA tensor")
+    s, c = torch.empty_like(x), torch.empty_like(x)
+    st = stream or torch.cuda.current_stream(x.device)
+    _check(lib.rd_joint_trig(RD_FLAG_FAST_TRIG if fast else 0, x.data_ptr(), s.data_ptr(),
+                             c.data_ptr(), x.numel(), ctypes.c_void_p(st.cuda_stream)))
+    return s, c
 
 
 def default_base(gravity=9.81):

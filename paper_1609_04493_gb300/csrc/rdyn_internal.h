@@ -18,6 +18,12 @@ struct rd_model {
     double *d_c64 = nullptr;  // same in FP64
     double TnR[9];            // joint frame of link n (for F_{n+1})
     double Tnp[3];
+    float *d_dh32 = nullptr;  // n * kDhConsts, common-normal-frame constants (FP32)
+    double *d_dh64 = nullptr; // same in FP64
+    double GBR[9];            // base frame D_{-1} of the common-normal frames in frame 0
+    double GBp[3];
+    double phi_last = 0;      // D_{n-1} is the joint frame of link n turned by phi_last about z
+    std::vector<double> host_dh64;  // the common-normal-frame constants on the host
     std::vector<double> host_c64;
     // device staging for the host-pointer entry points, grown on demand
     void *d_io = nullptr;
@@ -33,6 +39,15 @@ extern thread_local std::string g_rd_error;
 int rd_fail(int code, const char *fmt, ...);
 int rd_cuda_fail(cudaError_t e, const char *what);
 void rd_convert_base(const rd_model *m, const double *base, double out[18]);
+void rd_convert_base_dh(const rd_model *m, const double in18[18], double out[18]);
+int rd_build_dh(int n, const std::vector<double> &c64, std::vector<double> &dh64, double GBR[9],
+                double GBp[3], double *phi_last);
+int rd_rnea_dh_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                   void *tau, const double *base18, int stored, int block, int fast,
+                   int kfull, cudaStream_t s);
+int rd_rnea_dh_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                   void *tau, const double *base18, int stored, int block, int fast,
+                   int kfull, cudaStream_t s);
 int rd_rnea_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
                          const void *qdd, void *tau, const double *base18, int variant,
                          cudaStream_t s);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "rdyn_internal.h"
+#include "spatial_dh.cuh"
 
 thread_local std::string g_rd_error;
 
@@ -203,6 +204,108 @@ int rd_build_chain(int n, const double *M, const double *S, const double *inerti
     return RD_OK;
 }
 
+// Common-normal frames (spatial_dh.cuh) from the joint-frame constants: D_i is
+// joint frame i' turned about its z axis by phi_i so that its x axis lies along
+// z_i x z_{i+1} (phi_i = 0 for the last link and for parallel axes). Then the
+// constant part of f_{i-1,i}, Rz(-phi_{i-1}) (A_i, b_i) Rz(phi_i), is checked to
+// have the form (Rx(alpha_i) Rz(theta0_i), b_i'). D_{-1}, the base frame of the
+// recursion, is D_0 at q_0 = 0; GB is its pose in frame 0. Host-side, FP64.
+int rd_build_dh(int n, const std::vector<double> &c64, std::vector<double> &dh64, double GBR[9],
+                double GBp[3], double *phi_last)
+{
+    constexpr int J = rdyn::kLinkConsts, D = rdyn::kDhConsts;
+    std::vector<double> phi(n, 0.0);
+    for (int i = 0; i + 1 < n; ++i) {
+        const double *A = c64.data() + (size_t)(i + 1) * J;  // axis i+1 in frame i': A e_z
+        const double ux = A[2], uy = A[5];
+        if (std::hypot(ux, uy) > 1e-14) phi[i] = std::atan2(ux, -uy);
+    }
+    dh64.assign((size_t)n * D, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double *c = c64.data() + (size_t)i * J;
+        double *o = dh64.data() + (size_t)i * D;
+        const double cp = std::cos(phi[i]), sp = std::sin(phi[i]);
+        if (i == 0) {
+            o[0] = 1.0;  // alpha_0 = theta0_0 = 0, b_0 = 0
+        } else {
+            const double cm = std::cos(phi[i - 1]), sm = std::sin(phi[i - 1]);
+            // Q = Rz(-phi_{i-1}) A Rz(phi_i); bD = Rz(-phi_{i-1}) b
+            double T1[9], Q[9];
+            for (int r = 0; r < 3; ++r) {
+                const double *a = c + 3 * r;
+                T1[3 * r + 0] = a[0] * cp + a[1] * sp;
+                T1[3 * r + 1] = -a[0] * sp + a[1] * cp;
+                T1[3 * r + 2] = a[2];
+            }
+            for (int k = 0; k < 3; ++k) {
+                Q[0 + k] = cm * T1[0 + k] + sm * T1[3 + k];
+                Q[3 + k] = -sm * T1[0 + k] + cm * T1[3 + k];
+                Q[6 + k] = T1[6 + k];
+            }
+            const double b[3] = {c[9], c[10], c[11]};
+            const double bD[3] = {cm * b[0] + sm * b[1], -sm * b[0] + cm * b[1], b[2]};
+            double ca = Q[8], sa = -Q[5];
+            const double h = std::hypot(ca, sa);
+            ca /= h;
+            sa /= h;
+            // P = Rx(alpha)^T Q must be a rotation about z
+            double P[9];
+            for (int k = 0; k < 3; ++k) {
+                P[0 + k] = Q[0 + k];
+                P[3 + k] = ca * Q[3 + k] + sa * Q[6 + k];
+                P[6 + k] = -sa * Q[3 + k] + ca * Q[6 + k];
+            }
+            const double th0 = std::atan2(P[3], P[0]);
+            const double ct = std::cos(th0), st = std::sin(th0);
+            const double Rz[9] = {ct, -st, 0, st, ct, 0, 0, 0, 1};
+            double res = std::fabs(Q[2]);
+            for (int k = 0; k < 9; ++k) res = std::fmax(res, std::fabs(P[k] - Rz[k]));
+            if (!(res <= 1e-9))
+                return rd_fail(RD_ERR_ARG, "link %d: common-normal frame residual %g", i, res);
+            o[0] = ca;
+            o[1] = sa;
+            o[2] = bD[0];
+            o[3] = bD[1];
+            o[4] = bD[2];
+            o[5] = th0;
+        }
+        // inertia in D_i: c_D = Rz(-phi) c', I_D = Rz(-phi) I' Rz(phi)
+        o[6] = c[12];
+        const double cc[3] = {c[13], c[14], c[15]};
+        o[7] = cp * cc[0] + sp * cc[1];
+        o[8] = -sp * cc[0] + cp * cc[1];
+        o[9] = cc[2];
+        const double I[3][3] = {{c[16], c[19], c[20]}, {c[19], c[17], c[21]}, {c[20], c[21], c[18]}};
+        const double Rm[3][3] = {{cp, sp, 0}, {-sp, cp, 0}, {0, 0, 1}};  // Rz(-phi)
+        double ID[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int bb = 0; bb < 3; ++bb) {
+                double sum = 0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) sum += Rm[a][k] * I[k][l] * Rm[bb][l];
+                ID[a][bb] = sum;
+            }
+        o[10] = ID[0][0];
+        o[11] = ID[1][1];
+        o[12] = ID[2][2];
+        o[13] = 0.5 * (ID[0][1] + ID[1][0]);
+        o[14] = 0.5 * (ID[0][2] + ID[2][0]);
+        o[15] = 0.5 * (ID[1][2] + ID[2][1]);
+    }
+    // GB = (A_0 Rz(phi_0), b_0)
+    const double *c0 = c64.data();
+    const double cp = std::cos(phi[0]), sp = std::sin(phi[0]);
+    for (int r = 0; r < 3; ++r) {
+        const double *a = c0 + 3 * r;
+        GBR[3 * r + 0] = a[0] * cp + a[1] * sp;
+        GBR[3 * r + 1] = -a[0] * sp + a[1] * cp;
+        GBR[3 * r + 2] = a[2];
+        GBp[r] = c0[9 + r];
+    }
+    *phi_last = phi[n - 1];
+    return RD_OK;
+}
+
 extern "C" int rd_model_create(int n, const double *M, const double *S, const double *inertia,
                                rd_model **out)
 {
@@ -228,6 +331,14 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
     for (int k = 0; k < 9; ++k) mdl->TnR[k] = TnR[k];
     for (int k = 0; k < 3; ++k) mdl->Tnp[k] = Tnp[k];
     mdl->host_c64 = c64;
+    std::vector<double> dh64;
+    rc = rd_build_dh(n, c64, dh64, mdl->GBR, mdl->GBp, &mdl->phi_last);
+    if (rc) {
+        delete mdl;
+        return rc;
+    }
+    std::vector<float> dh32(dh64.begin(), dh64.end());
+    mdl->host_dh64 = dh64;
 
     std::vector<float> c32(c64.size());
     for (size_t k = 0; k < c64.size(); ++k) c32[k] = (float)c64[k];
@@ -236,6 +347,12 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
     if (e == cudaSuccess) e = cudaMalloc(&mdl->d_c32, b32);
     if (e == cudaSuccess) e = cudaMemcpy(mdl->d_c64, c64.data(), b64, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(mdl->d_c32, c32.data(), b32, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&mdl->d_dh64, dh64.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&mdl->d_dh32, dh32.size() * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(mdl->d_dh64, dh64.data(), dh64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(mdl->d_dh32, dh32.data(), dh32.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         rd_model_destroy(mdl);
         return e == cudaErrorMemoryAllocation ? rd_fail(RD_ERR_ALLOC, "rd_model_create: %s",
@@ -254,6 +371,8 @@ extern "C" void rd_model_destroy(rd_model *m)
     if (prev != m->device) cudaSetDevice(m->device);
     if (m->d_c32) cudaFree(m->d_c32);
     if (m->d_c64) cudaFree(m->d_c64);
+    if (m->d_dh32) cudaFree(m->d_dh32);
+    if (m->d_dh64) cudaFree(m->d_dh64);
     if (m->d_io) cudaFree(m->d_io);
     if (m->io_in) cudaStreamDestroy(m->io_in);
     if (m->io_out) cudaStreamDestroy(m->io_out);
@@ -284,5 +403,29 @@ void rd_convert_base(const rd_model *m, const double *base, double out[18])
         }
         out[12 + a] = sf;
         out[15 + a] = sn;
+    }
+}
+
+// Boundary terms in the common-normal frames, from those of rd_convert_base:
+// V_0 and dV_0 move from frame 0 to D_{-1} (Ad_{GB^-1}: (R^T (v + w x p), R^T w)),
+// F_{n+1} turns by -phi_last about z (D_{n-1} shares its origin with n').
+void rd_convert_base_dh(const rd_model *m, const double in18[18], double out[18])
+{
+    const double *R = m->GBR, *p = m->GBp;
+    for (int t = 0; t < 2; ++t) {
+        const double *v = in18 + 6 * t, *w = in18 + 6 * t + 3;
+        const double u[3] = {v[0] + w[1] * p[2] - w[2] * p[1], v[1] + w[2] * p[0] - w[0] * p[2],
+                             v[2] + w[0] * p[1] - w[1] * p[0]};
+        for (int a = 0; a < 3; ++a) {
+            out[6 * t + a] = R[a] * u[0] + R[3 + a] * u[1] + R[6 + a] * u[2];
+            out[6 * t + 3 + a] = R[a] * w[0] + R[3 + a] * w[1] + R[6 + a] * w[2];
+        }
+    }
+    const double c = std::cos(m->phi_last), s = std::sin(m->phi_last);
+    for (int t = 0; t < 2; ++t) {
+        const double *x = in18 + 12 + 3 * t;
+        out[12 + 3 * t + 0] = c * x[0] + s * x[1];
+        out[12 + 3 * t + 1] = -s * x[0] + c * x[1];
+        out[12 + 3 * t + 2] = x[2];
     }
 }

@@ -1,0 +1,234 @@
+// rnea_dh_launch.cuh -- launches of the common-normal-frame RNEA kernels
+// (rnea_dh.cuh); included once per element type (rnea_dh_f32.cu,
+// rnea_dh_f64.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "rdyn_internal.h"
+#include "rnea_dhp.cuh"
+
+namespace rdyn {
+namespace {
+
+int dh_smem_optin(int device)
+{
+    static std::atomic<int> cache[64];
+    if (device < 0 || device >= 64) return 48 * 1024;
+    int v = cache[device].load();
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+            cudaSuccess)
+            v = 48 * 1024;
+        cache[device].store(v);
+    }
+    return v;
+}
+
+template <typename T>
+size_t dh_smem(int n, int block, int mode, bool vec)
+{
+    size_t s = (size_t)n * kDhConsts * sizeof(T);
+    if (vec) s += (size_t)stage_bytes_per_thread<T>() * block;
+    s += (size_t)n * state_bytes_per_link<T>(mode) * block;
+    return s;
+}
+
+template <typename T, int BLOCK, int MODE, bool VEC, bool FAST>
+int launch_dh_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                void *tau, const BaseParams<T> &base, size_t smem, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    auto kern = rnea_dh_kernel<T, BLOCK, MODE, VEC, FAST>;
+    const uint64_t bit = 1ull << (m->device & 63);
+    if (!(configured.load() & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             dh_smem_optin(m->device));
+        if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+        configured.fetch_or(bit);
+    }
+    const T *consts = nullptr;
+    if constexpr (sizeof(T) == 4) consts = m->d_dh32;
+    else consts = m->d_dh64;
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    kern<<<grid, BLOCK, smem, stream>>>(consts, m->n, B, static_cast<const T *>(q),
+                                        static_cast<const T *>(qd), static_cast<const T *>(qdd),
+                                        static_cast<T *>(tau), base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea common-normal kernel launch");
+    return RD_OK;
+}
+
+inline bool dh_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename T, int BLOCK, int MODE>
+int launch_dh_b(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                void *tau, const BaseParams<T> &base, bool fast, cudaStream_t s)
+{
+    const size_t limit = (size_t)dh_smem_optin(m->device);
+    const bool vec = (m->n % 4 == 0) && dh_aligned16(q) && dh_aligned16(qd) &&
+                     dh_aligned16(qdd) && dh_aligned16(tau) &&
+                     dh_smem<T>(m->n, BLOCK, MODE, true) <= limit;
+    const size_t smem = dh_smem<T>(m->n, BLOCK, MODE, vec);
+    if (smem > limit)
+        return rd_fail(RD_ERR_ARG, "rnea_batch: %zu bytes of shared memory needed, %zu available",
+                       smem, limit);
+    if constexpr (sizeof(T) == 4) {
+        if (fast)
+            return vec ? launch_dh_k<T, BLOCK, MODE, true, true>(m, B, q, qd, qdd, tau, base, smem, s)
+                       : launch_dh_k<T, BLOCK, MODE, false, true>(m, B, q, qd, qdd, tau, base, smem, s);
+    }
+    return vec ? launch_dh_k<T, BLOCK, MODE, true, false>(m, B, q, qd, qdd, tau, base, smem, s)
+               : launch_dh_k<T, BLOCK, MODE, false, false>(m, B, q, qd, qdd, tau, base, smem, s);
+}
+
+template <typename T, int MODE>
+int launch_dh_mode(const rd_model *m, int block, int B, const void *q, const void *qd,
+                   const void *qdd, void *tau, const BaseParams<T> &base, bool fast,
+                   cudaStream_t s)
+{
+    switch (block) {
+    case 32: return launch_dh_b<T, 32, MODE>(m, B, q, qd, qdd, tau, base, fast, s);
+    case 64: return launch_dh_b<T, 64, MODE>(m, B, q, qd, qdd, tau, base, fast, s);
+    case 128: return launch_dh_b<T, 128, MODE>(m, B, q, qd, qdd, tau, base, fast, s);
+    default: return rd_fail(RD_ERR_ARG, "rnea_batch: block size %d not built (32, 64, 128)", block);
+    }
+}
+
+template <typename T, int NMAX, int BLOCK, int TRIG>
+int launch_dhp_k(const rd_model *m, int K, int B, const void *q, const void *qd, const void *qdd,
+                 void *tau, const BaseParams<T> &base, size_t smem, cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    auto kern = rnea_dhp_kernel<T, NMAX, BLOCK, TRIG>;
+    const uint64_t bit = 1ull << (m->device & 63);
+    if (!(configured.load() & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             dh_smem_optin(m->device));
+        if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+        configured.fetch_or(bit);
+    }
+    DhParamConsts<T, NMAX> pc;
+    for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (T)m->host_dh64[k];
+    for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = T(0);
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    kern<<<grid, BLOCK, smem, stream>>>(pc, m->n, K, B, static_cast<const T *>(q),
+                                        static_cast<const T *>(qd), static_cast<const T *>(qdd),
+                                        static_cast<T *>(tau), base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea common-normal kernel launch");
+    return RD_OK;
+}
+
+template <typename T, int NMAX, int TRIG>
+int launch_dhp_b(const rd_model *m, int block, int K, int B, const void *q, const void *qd,
+                 const void *qdd, void *tau, const BaseParams<T> &base, size_t smem,
+                 cudaStream_t s)
+{
+    switch (block) {
+    case 32: return launch_dhp_k<T, NMAX, 32, TRIG>(m, K, B, q, qd, qdd, tau, base, smem, s);
+    case 64: return launch_dhp_k<T, NMAX, 64, TRIG>(m, K, B, q, qd, qdd, tau, base, smem, s);
+    case 128: return launch_dhp_k<T, NMAX, 128, TRIG>(m, K, B, q, qd, qdd, tau, base, smem, s);
+    default: return rd_fail(RD_ERR_ARG, "rnea_batch: block size %d not built (32, 64, 128)", block);
+    }
+}
+
+int dh_device_attr(int device, cudaDeviceAttr attr, int fallback)
+{
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, attr, device) != cudaSuccess || v <= 0) return fallback;
+    return v;
+}
+
+// Default K for the parameter-constant kernel (32-thread blocks). On GB300 at
+// B = 65536 the fastest K at every length was the largest that still leaves 7
+// blocks per SM, so the batch runs in at most two waves (n = 16: K = 16, 10.8 us;
+// n = 32: K = 24, 23.2 us; n = 64: K = 12, 46.7 us; n = 100: K = 0, 71.2 us,
+// against 14.8 / 29.7 / 60.2 / 92.0 us for the joint-frame kernels). When the
+// whole batch fits in one wave with more state, the larger K is taken.
+template <typename T>
+int dhp_default_k(const rd_model *m, int B)
+{
+    static std::atomic<int> smem_sm[64], sms[64];
+    const int d = m->device & 63;
+    if (smem_sm[d].load() == 0) {
+        smem_sm[d].store(dh_device_attr(m->device, cudaDevAttrMaxSharedMemoryPerMultiprocessor, 100 * 1024));
+        sms[d].store(dh_device_attr(m->device, cudaDevAttrMultiProcessorCount, 1));
+    }
+    const int n = m->n;
+    auto blocks_per_sm = [&](int K) {
+        const size_t per_block = dhp_smem_per_thread<T>(n, K) * 32 + 1024;  // + the block's reserve
+        const long long b = (long long)smem_sm[d].load() / (long long)per_block;
+        return b > 32 ? 32 : (int)b;
+    };
+    const long long blocks = (B + 31) / 32;
+    int best = 0;
+    for (int K = 0; K <= n; K += 4) {
+        const int per_sm = blocks_per_sm(K);
+        if (per_sm >= 7 || (long long)per_sm * sms[d].load() >= blocks) best = K;
+    }
+    return best;
+}
+
+// Parameter-constant kernel with full state for the first K links (K a multiple
+// of 4, at most n; K < 0: library default); needs n % 4 == 0, n <= 128 and
+// 16-byte aligned rows.
+template <typename T>
+bool dhp_eligible(const rd_model *m, const void *q, const void *qd, const void *qdd,
+                  const void *tau)
+{
+    return m->n % 4 == 0 && m->n <= 128 && dh_aligned16(q) && dh_aligned16(qd) &&
+           dh_aligned16(qdd) && dh_aligned16(tau);
+}
+
+template <typename T>
+int launch_dhp(const rd_model *m, int block, int K, int B, const void *q, const void *qd,
+               const void *qdd, void *tau, const BaseParams<T> &base, bool fast, cudaStream_t s)
+{
+    const int n = m->n;
+    if (K < 0) K = dhp_default_k<T>(m, B);
+    K = K > n ? n : 4 * (K / 4);
+    const size_t smem = dhp_smem_per_thread<T>(n, K) * (size_t)block;
+    if (smem > (size_t)dh_smem_optin(m->device))
+        return rd_fail(RD_ERR_ARG, "rnea_batch: state of %d links needs %zu bytes of shared "
+                                   "memory, %d available", K, smem, dh_smem_optin(m->device));
+    const bool sfu = sizeof(T) == 4 && fast;
+    if (n <= 32)
+        return sfu ? launch_dhp_b<T, 32, kTrigSfu>(m, block, K, B, q, qd, qdd, tau, base, smem, s)
+                   : launch_dhp_b<T, 32, kTrigPoly>(m, block, K, B, q, qd, qdd, tau, base, smem, s);
+    return sfu ? launch_dhp_b<T, 128, kTrigSfu>(m, block, K, B, q, qd, qdd, tau, base, smem, s)
+               : launch_dhp_b<T, 128, kTrigPoly>(m, block, K, B, q, qd, qdd, tau, base, smem, s);
+}
+
+// stored: state for the first K links (kfull; < 0 = library default), else
+// none. Rows with n % 4 == 0, n <= 128 and 16-byte alignment take the
+// parameter-constant kernel; others the shared-memory-constant kernel, with
+// every link's state (stored) or none.
+template <typename T>
+int dh_launch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+              void *tau, const double *base18, bool stored, int block, bool fast, int kfull,
+              cudaStream_t s)
+{
+    double b[18];
+    rd_convert_base_dh(m, base18, b);
+    BaseParams<T> base;
+    for (int k = 0; k < 6; ++k) {
+        base.V0[k] = (T)b[k];
+        base.dV0[k] = (T)b[6 + k];
+        base.Fn[k] = (T)b[12 + k];
+    }
+    if (dhp_eligible<T>(m, q, qd, qdd, tau))
+        return launch_dhp<T>(m, block ? block : 32, stored ? kfull : 0, B, q, qd, qdd, tau, base,
+                             fast, s);
+    if (stored) {
+        if (!block)
+            block = dh_smem<T>(m->n, 64, kStore, true) <= (size_t)dh_smem_optin(m->device) / 4 ? 64 : 32;
+        return launch_dh_mode<T, kStore>(m, block, B, q, qd, qdd, tau, base, fast, s);
+    }
+    return launch_dh_mode<T, kRecompute>(m, block ? block : 64, B, q, qd, qdd, tau, base, fast, s);
+}
+
+}  // namespace
+}  // namespace rdyn

@@ -290,7 +290,11 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     if (block) block = 1 << block;
     const int reglinks = 4 * ((variant >> 20) & 0xff);  // RD_TUNE_REGLINKS / _STORED_LINKS
     variant &= 0xfff;
-    if (variant == RD_VARIANT_AUTO && B <= 152 * 32 && n <= 128) {
+    const bool dhp_rows = sizeof(T) == 4 && n % 4 == 0 && n <= 128 && aligned16(q) &&
+                          aligned16(qd) && aligned16(qdd) && aligned16(tau);
+    // the common-normal kernel of the next branch overtakes the scans sooner
+    // (n = 32: 7.5 us against 9.3 at B = 4096; 6.9 against 5.0 at B = 1024)
+    if (variant == RD_VARIANT_AUTO && B <= (dhp_rows ? 2048 : 152 * 32) && n <= 128) {
         // Fewer instances than one warp per SM: the serial recursion leaves the
         // GPU idle, and splitting each chain over lanes (the scans of Sec. III)
         // cuts latency. Measured: n = 7, B = 1024 FP64 30 us with 8 lanes vs 43
@@ -303,6 +307,13 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
             if (fast) return launch_scan<T, true>(m, lanes, B, q, qd, qdd, tau, base18, s);
         }
         return launch_scan<T, false>(m, lanes, B, q, qd, qdd, tau, base18, s);
+    }
+    if (variant == RD_VARIANT_AUTO && dhp_rows) {
+        // FP32, whole 16-byte chunks: common-normal frames, constants as a kernel
+        // parameter, full state for the library's K (about 22% below the
+        // joint-frame kernels at n = 16..100, B = 65536; see rnea_dh_launch.cuh)
+        return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, 1, block, fast,
+                              reglinks ? reglinks : -1, s);
     }
     if (variant == RD_VARIANT_AUTO) {
         // Sweep on GB300 at B = 65536 (modes x block sizes x stored links):
@@ -345,6 +356,14 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     }
     if (variant == RD_VARIANT_SERIAL_REGSTATE)
         return launch_regstate<T>(m, block, reglinks, B, q, qd, qdd, tau, base18, fast, s);
+    if (variant == RD_VARIANT_SERIAL_DH || variant == RD_VARIANT_SERIAL_DH_RECOMPUTE) {
+        const int stored = variant == RD_VARIANT_SERIAL_DH;
+        const int kfull = reglinks ? reglinks : -1;
+        if constexpr (sizeof(T) == 4)
+            return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, s);
+        else
+            return rd_rnea_dh_f64(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, s);
+    }
     if (variant == RD_VARIANT_SERIAL_HYBRID) {
         if (!block) block = 32;
         const int K = reglinks ? reglinks : 16;
