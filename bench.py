@@ -37,12 +37,38 @@ METRIC = "RNEA evals/s at n=32,B=65536 FP32 vs FP64; adjoint evals/s; % of roofl
 UNIT = "evals/s"
 WORKLOAD = "rnea_n32_B65536"
 ROTATE = 8  # input sets cycled between steps; 8 x 33.5 MB > 2 x L2 (129 MB)
-FLOP_PER_LINK = 274     # arithmetic of the joint-frame formulation per link, FMA = 2:
-                        # rotation 18 + forward step 94 + bias wrench 102 + carry 60
+# Algorithmic arithmetic of one link of the recursion of Sec. II-A with general
+# link transforms, FMA = 2: transform f = M exp(S q) by the Rodrigues formula and
+# a 3x4 compose (~135), forward step (~150), bias wrench (~125), backward step
+# (~50), torque (~11). The roofline's "achieved" divides this fixed count by
+# the measured time; the kernel's own count is reported beside it.
+ALGO_FLOP_PER_LINK = 470
+# Executed arithmetic of the joint-frame kernels per link (FMA = 2): rotation 18
+# + forward step 94 + bias wrench 102 + carry 60.
+JOINT_FRAME_FLOP_PER_LINK = 274
+
+
+def dh_param_flops(n, K):
+    """Executed arithmetic (FMA = 2) of one instance in the common-normal kernel
+    with full state for links 0..K-1: a stored link costs sin/cos 26 + rotation
+    products 4 + forward step 86 + bias wrench 102 + backward carry 44 + products 4;
+    a link without full state adds the re-derivation of its motion (86) and
+    moves its bias wrench to the backward sweep; the top link adds instead of
+    carrying (-38) and the lowest re-derived link needs no inverse step (-86)."""
+    stored, rederived = 266, 352
+    total = K * stored + (n - K) * rederived - 38
+    if K < n:
+        total -= 86
+    return total
+
+
 # adjoint arithmetic per link (FMA = 2): sweep 1 155 (rotation, motion, wrench
 # adjoint), sweep 2 500 (bias wrench, carries, inertia products, ad terms,
 # gradients) plus 137 to re-derive the motion and wrench adjoint (recompute mode)
 VJP_FLOP_PER_LINK = {1: 655, 2: 792}
+# algorithmic arithmetic of the adjoint per link: about three inverse-dynamics
+# passes of the general formulation above
+VJP_ALGO_FLOP_PER_LINK = 1400
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
@@ -172,7 +198,8 @@ def recorded_traffic(kernel_tag):
 
 # Sources that define the headline kernel's code: a profile summary is matched
 # to them, so its counters go stale when the kernel changes.
-RNEA_KERNEL_SOURCES = ("spatial.cuh", "rnea_serial.cuh")
+RNEA_KERNEL_SOURCES = ("spatial.cuh", "spatial_dh.cuh", "rnea_serial.cuh", "rnea_dh.cuh",
+                       "rnea_dhp.cuh", "trig_poly.cuh")
 
 
 def kernel_sources_hash(files=RNEA_KERNEL_SOURCES):
@@ -270,11 +297,14 @@ def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
         t = time_calls(torch, call, steps, 3, dist, sampler)
         name = f"B{B}_{'store' if mode == rd.RD_VJP_STORE else 'recompute'}"
         fpl = VJP_FLOP_PER_LINK[mode]
-        tf = B * N_LINKS * fpl / (t / steps) / 1e12
+        tf = B * N_LINKS * VJP_ALGO_FLOP_PER_LINK / (t / steps) / 1e12
+        tx = B * N_LINKS * fpl / (t / steps) / 1e12
         peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
         out[name] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
-                     "steps": steps, "flop_per_link": fpl, "achieved_tflops": tf,
-                     "frac_of_fp32_peak": tf / peak32}
+                     "steps": steps, "flop_per_link": VJP_ALGO_FLOP_PER_LINK,
+                     "achieved_tflops": tf, "frac_of_fp32_peak": tf / peak32,
+                     "executed_flop_per_link": fpl, "executed_tflops": tx,
+                     "executed_frac_of_fp32_peak": tx / peak32}
     out["metric"] = "RNEA adjoint d(w^T tau)/d(q, qd, qdd) evals/s, n=32 FP32"
     return out
 
@@ -391,10 +421,19 @@ def run_ours(args):
            "gpu_launches": K}
 
     # roofline of the dominant kernel (the FP32 RNEA kernel: one launch per step)
+    kern_id, kern_block, kern_stored = rd.rnea_last_config()
+    if kern_id == rd.RD_RNEA_KERNEL_DH_PARAM:
+        kname = (f"rnea_dhp_kernel<float, {kern_block} threads>, common-normal frames, "
+                 f"constants as a kernel parameter, full state for {kern_stored} of "
+                 f"{N_LINKS} links, polynomial sin/cos")
+        exec_fpl = dh_param_flops(N_LINKS, kern_stored) / N_LINKS
+    else:
+        kname = f"rnea kernel family {kern_id:#x}, {kern_block} threads"
+        exec_fpl = JOINT_FRAME_FLOP_PER_LINK
     avg_launch = t32 / K
-    flops = FLOP_PER_LINK * N_LINKS * BATCH
     peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
-    achieved = flops / avg_launch / 1e12
+    achieved = ALGO_FLOP_PER_LINK * N_LINKS * BATCH / avg_launch / 1e12
+    executed = exec_fpl * N_LINKS * BATCH / avg_launch / 1e12
     traffic = recorded_traffic("rnea_fp32_n32_B65536")
     try:
         fma32 = rd.measure_fma_peak("float32")
@@ -403,8 +442,12 @@ def run_ours(args):
         fma32 = fma64 = None
     res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                        "frac": achieved / peak32, "traffic": traffic,
-                       "kernel": "rnea_serial_kernel<float, 32 threads, shared-memory state>",
-                       "flop_per_link": FLOP_PER_LINK,
+                       "kernel": kname, "avg_launch_us": avg_launch * 1e6,
+                       "flop_per_link": ALGO_FLOP_PER_LINK,
+                       "flop_count": "algorithmic: the recursion of Sec. II-A with general link "
+                                     "transforms (Rodrigues exponential and 3x4 compose), FMA = 2",
+                       "executed_flop_per_link": exec_fpl,
+                       "executed_tflops": executed, "executed_frac": executed / peak32,
                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                        "measured_fma_tflops": {"fp32": fma32, "fp64": fma64},
                        "hbm": {"algorithmic_bytes_per_launch": BATCH * N_LINKS * 16,
@@ -422,11 +465,15 @@ def run_ours(args):
         torch.cuda.synchronize()
         g64 = capture(torch, rd, model, sets64, K64)
         t64 = max_over_ranks(dist, timed_graph(torch, g64, dist, sampler))
-        fp64_flops = FLOP_PER_LINK * N_LINKS * BATCH / (t64 / K64) / 1e12
+        k64 = rd.rnea_last_config()
+        fp64_flops = ALGO_FLOP_PER_LINK * N_LINKS * BATCH / (t64 / K64) / 1e12
+        fp64_exec = JOINT_FRAME_FLOP_PER_LINK * N_LINKS * BATCH / (t64 / K64) / 1e12
         res["fp64"] = {"value": world * BATCH * K64 / t64, "unit": UNIT, "steps": K64,
-                       "ms_per_step": t64 / K64 * 1e3, "achieved_tflops": fp64_flops,
+                       "ms_per_step": t64 / K64 * 1e3, "kernel_family": k64[0],
+                       "achieved_tflops": fp64_flops, "executed_tflops": fp64_exec,
                        "peak_tflops_nominal": FP64_NOMINAL_TFLOPS,
                        "frac_of_nominal": fp64_flops / FP64_NOMINAL_TFLOPS,
+                       "executed_frac_of_nominal": fp64_exec / FP64_NOMINAL_TFLOPS,
                        "frac_of_measured_fma": (fp64_flops / fma64) if fma64 else None,
                        "fp32_over_fp64": value / (world * BATCH * K64 / t64)}
         del g64, gw64, sets64

@@ -369,6 +369,22 @@ int rd_measure_fma_peak(int dtype, double *tflops, void *stream);
  */
 int rd_joint_trig(int flags, const float *x, float *s, float *c, int count, void *stream);
 
+/*
+ * rd_rnea_last_config -- the kernel the calling thread's last rnea_batch call
+ * launched (a diagnostic for tuning and benchmarks):
+ *   kernel        an rd_variant value naming the kernel family (RD_VARIANT_SERIAL,
+ *                 ..._RECOMPUTE, ..._RECOMPUTE_CS, ..._REGSTATE, ..._HYBRID,
+ *                 RD_VARIANT_SERIAL_DH, ..._DH_RECOMPUTE with shared-memory
+ *                 constants, RD_VARIANT_SCAN(L)) or RD_RNEA_KERNEL_DH_PARAM for
+ *                 the common-normal kernel with its constants as a kernel
+ *                 parameter;
+ *   block         threads per block;
+ *   stored_links  links whose full backward-sweep state the kernel keeps.
+ * All 0 before the first launch on this thread. Errors: RD_ERR_ARG (null output).
+ */
+#define RD_RNEA_KERNEL_DH_PARAM 0x206
+int rd_rnea_last_config(int *kernel, int *block, int *stored_links);
+
 /* Message for the last error on the calling thread ("" if none). */
 const char *rd_last_error(void);
 

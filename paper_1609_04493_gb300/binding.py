@@ -121,6 +121,9 @@ def load(build_if_missing=True):
         lib.rd_measure_fma_peak.restype = I
         lib.rd_joint_trig.argtypes = [I, P, P, P, I, P]
         lib.rd_joint_trig.restype = I
+        IP = ctypes.POINTER(ctypes.c_int)
+        lib.rd_rnea_last_config.argtypes = [IP, IP, IP]
+        lib.rd_rnea_last_config.restype = I
         _lib = lib
         return lib
 
@@ -144,6 +147,17 @@ def measure_fma_peak(dtype="float32", stream=None):
     _check(lib.rd_measure_fma_peak(RD_F32 if dtype == "float32" else RD_F64, ctypes.byref(out),
                                    ctypes.c_void_p(st.cuda_stream)))
     return out.value
+
+
+RD_RNEA_KERNEL_DH_PARAM = 0x206
+
+
+def rnea_last_config():
+    """(kernel, block, stored_links) of this thread's last rnea_batch launch."""
+    lib = load()
+    k, b, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib.rd_rnea_last_config(ctypes.byref(k), ctypes.byref(b), ctypes.byref(s)))
+    return k.value, b.value, s.value
 
 
 def joint_trig(x, fast=False, stream=None):

@@ -36,6 +36,18 @@ struct rd_model {
 };
 
 extern thread_local std::string g_rd_error;
+// Kernel, block size and stored links of the calling thread's last rnea_batch
+// launch (rd_rnea_last_config).
+struct RdLaunchConfig {
+    int kernel = 0, block = 0, stored_links = 0;
+};
+extern thread_local RdLaunchConfig g_rd_last_rnea;
+inline void rd_note_rnea(int kernel, int block, int stored)
+{
+    g_rd_last_rnea.kernel = kernel;
+    g_rd_last_rnea.block = block;
+    g_rd_last_rnea.stored_links = stored;
+}
 int rd_fail(int code, const char *fmt, ...);
 int rd_cuda_fail(cudaError_t e, const char *what);
 void rd_convert_base(const rd_model *m, const double *base, double out[18]);

@@ -25,6 +25,17 @@
 #include "spatial_dh.cuh"
 
 thread_local std::string g_rd_error;
+thread_local RdLaunchConfig g_rd_last_rnea;
+
+extern "C" int rd_rnea_last_config(int *kernel, int *block, int *stored_links)
+{
+    if (!kernel || !block || !stored_links)
+        return rd_fail(RD_ERR_ARG, "rd_rnea_last_config: null output");
+    *kernel = g_rd_last_rnea.kernel;
+    *block = g_rd_last_rnea.block;
+    *stored_links = g_rd_last_rnea.stored_links;
+    return RD_OK;
+}
 
 int rd_fail(int code, const char *fmt, ...)
 {

@@ -53,6 +53,8 @@ int launch_dh_k(const rd_model *m, int B, const void *q, const void *qd, const v
     if constexpr (sizeof(T) == 4) consts = m->d_dh32;
     else consts = m->d_dh64;
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    rd_note_rnea(MODE == kStore ? RD_VARIANT_SERIAL_DH : RD_VARIANT_SERIAL_DH_RECOMPUTE, BLOCK,
+                 MODE == kStore ? m->n : 0);
     kern<<<grid, BLOCK, smem, stream>>>(consts, m->n, B, static_cast<const T *>(q),
                                         static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                         static_cast<T *>(tau), base);
@@ -114,6 +116,7 @@ int launch_dhp_k(const rd_model *m, int K, int B, const void *q, const void *qd,
     for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (T)m->host_dh64[k];
     for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = T(0);
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    rd_note_rnea(RD_RNEA_KERNEL_DH_PARAM, BLOCK, K);
     kern<<<grid, BLOCK, smem, stream>>>(pc, m->n, K, B, static_cast<const T *>(q),
                                         static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                         static_cast<T *>(tau), base);

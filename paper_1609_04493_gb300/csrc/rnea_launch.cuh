@@ -77,6 +77,9 @@ int launch_serial_k(const rd_model *m, int B, const void *q, const void *qd, con
     if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
     else consts = reinterpret_cast<const T *>(m->d_c64);
     unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    rd_note_rnea(MODE == kStore ? RD_VARIANT_SERIAL : MODE == kRecompute ? RD_VARIANT_SERIAL_RECOMPUTE
+                                                                        : RD_VARIANT_SERIAL_RECOMPUTE_CS,
+                 BLOCK, MODE == kStore ? n : 0);
     kern<<<grid, BLOCK, smem, stream>>>(consts, n, B, static_cast<const T *>(q),
                                         static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                         static_cast<T *>(tau), make_base<T>(base18));
@@ -134,6 +137,7 @@ int launch_hybrid_k(const rd_model *m, int K, int B, const void *q, const void *
     if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
     else consts = reinterpret_cast<const T *>(m->d_c64);
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    rd_note_rnea(RD_VARIANT_SERIAL_HYBRID, BLOCK, K);
     kern<<<grid, BLOCK, smem, stream>>>(consts, n, K, B, static_cast<const T *>(q),
                                         static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                         static_cast<T *>(tau), make_base<T>(base18));
@@ -193,6 +197,7 @@ int launch_scan_k(const rd_model *m, int B, const void *q, const void *qd, const
     else consts = reinterpret_cast<const T *>(m->d_c64);
     const long long threads = (long long)B * L;
     const unsigned grid = (unsigned)((threads + 127) / 128);
+    rd_note_rnea(RD_VARIANT_SCAN(L), 128, 0);
     kern<<<grid, 128, smem, stream>>>(consts, n, B, static_cast<const T *>(q),
                                       static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                       static_cast<T *>(tau), make_base<T>(base18));
@@ -246,6 +251,7 @@ int launch_regstate_k(const rd_model *m, int B, const void *q, const void *qd, c
     if constexpr (sizeof(T) == 4) consts = reinterpret_cast<const T *>(m->d_c32);
     else consts = reinterpret_cast<const T *>(m->d_c64);
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    rd_note_rnea(RD_VARIANT_SERIAL_REGSTATE, BLOCK, n);
     kern<<<grid, BLOCK, smem, stream>>>(consts, n, B, static_cast<const T *>(q),
                                         static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                         static_cast<T *>(tau), make_base<T>(base18));
