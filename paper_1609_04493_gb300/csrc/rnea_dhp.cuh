@@ -38,7 +38,8 @@ __device__ __forceinline__ void dh_trig(T x, T *s, T *c)
     else sincos_poly(x, s, c);
 }
 
-// The backward sweep stages qd and qdd only (slots of the forward ring).
+// The backward sweep needs qd and qdd only; they sit at positions 1 and 2 of
+// the forward ring's slots.
 template <typename T, int BLOCK>
 __device__ __forceinline__ void stage_chunk2(unsigned char *ring, int slot, int tid,
                                              const T *qdr, const T *qddr, int i0)
@@ -50,7 +51,7 @@ __device__ __forceinline__ void stage_chunk2(unsigned char *ring, int slot, int 
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int h = 0; h < P; ++h)
-            __pipeline_memcpy_async(&r[((slot * 3 + a) * P + h) * BLOCK + tid],
+            __pipeline_memcpy_async(&r[((slot * 3 + a + 1) * P + h) * BLOCK + tid],
                                     src[a] + i0 + h * (16 / (int)sizeof(T)), 16);
 }
 
@@ -65,7 +66,7 @@ __device__ __forceinline__ void read_chunk2(const unsigned char *ring, int slot,
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int h = 0; h < P; ++h) {
-            float4 v = r[((slot * 3 + a) * P + h) * BLOCK + tid];
+            float4 v = r[((slot * 3 + a + 1) * P + h) * BLOCK + tid];
             if constexpr (sizeof(T) == 4) {
                 dst[a]->v[0] = v.x; dst[a]->v[1] = v.y; dst[a]->v[2] = v.z; dst[a]->v[3] = v.w;
             } else {
@@ -162,18 +163,20 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
     V3<T> bn = mk3(T(0), T(0), T(0));
     const int last0 = n - 4;
     const int nrc = nchunks - kchunks;
-#pragma unroll
-    for (int k = 0; k < kStages - 1; ++k) {
-        if (k < nrc) stage_chunk2<T, BLOCK>(ring, k, tid, qdr, qddr, last0 - 4 * k);
-        __pipeline_commit();
-    }
+    // Forward chunk c was staged in slot c % kStages and is only overwritten by
+    // chunk c + kStages, so the ring still holds the last kStages chunks: the
+    // backward sweep reads those in place and stages older ones kStages - 1
+    // steps ahead, each into the slot of the chunk read one step before.
     for (int kb = 0; kb < nrc; ++kb) {
         const int i0 = last0 - 4 * kb;
         const int ahead = kb + kStages - 1;
-        if (ahead < nrc) stage_chunk2<T, BLOCK>(ring, ahead % kStages, tid, qdr, qddr, last0 - 4 * ahead);
+        if (ahead >= kStages && ahead < nrc) {
+            const int c = nchunks - 1 - ahead;
+            stage_chunk2<T, BLOCK>(ring, c % kStages, tid, qdr, qddr, 4 * c);
+        }
         __pipeline_commit();
         __pipeline_wait_prior(kStages - 1);
-        read_chunk2<T, BLOCK>(ring, kb % kStages, tid, cqd, cqdd);
+        read_chunk2<T, BLOCK>(ring, (nchunks - 1 - kb) % kStages, tid, cqd, cqdd);
         Chunk<T> ct;
 #pragma unroll
         for (int j = 3; j >= 0; --j) {
