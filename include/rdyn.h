@@ -179,12 +179,18 @@ int rnea_batch_host(rd_model *model, int B, int dtype, const void *q, const void
                     const void *qdd, void *tau, const double *base, int variant,
                     void *stream);
 
-/* Modes of rnea_vjp (OR-able with RD_FLAG_FAST_TRIG). */
+/* Modes of rnea_vjp (OR-able with RD_FLAG_FAST_TRIG and RD_VJP_FLAG_JOINT_FRAMES).
+ * Rows with n % 4 == 0, n <= 128 and 16-byte aligned arrays run in the
+ * common-normal link frames of RD_VARIANT_SERIAL_DH, with the link constants as
+ * a kernel parameter; other rows in the joint frames. */
 enum rd_vjp_mode {
     RD_VJP_AUTO = 0,      /* library's choice (FP64 with a large enough workspace: store) */
     RD_VJP_STORE = 1,     /* keep the forward sweep's state in the workspace */
     RD_VJP_RECOMPUTE = 2  /* keep nothing: re-derive it by inverting the forward step */
 };
+/* OR-able into the mode of rnea_vjp: run the joint-frame kernel even where the
+ * common-normal one applies (for comparisons). */
+#define RD_VJP_FLAG_JOINT_FRAMES 0x2000
 
 /*
  * rnea_vjp -- vector-Jacobian product of inverse dynamics for B states:

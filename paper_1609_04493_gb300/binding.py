@@ -26,6 +26,7 @@ RD_FLAG_FAST_TRIG = 0x1000
 RD_VJP_AUTO = 0
 RD_VJP_STORE = 1
 RD_VJP_RECOMPUTE = 2
+RD_VJP_FLAG_JOINT_FRAMES = 0x2000
 
 
 def RD_VARIANT_SCAN(lanes):

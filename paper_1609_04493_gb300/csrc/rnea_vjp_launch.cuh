@@ -8,6 +8,7 @@
 
 #include "rdyn_internal.h"
 #include "rnea_vjp.cuh"
+#include "rnea_vjp_dh.cuh"
 
 namespace rdyn {
 namespace {
@@ -74,12 +75,71 @@ int launch_vjp_mode(const rd_model *m, int B, const void *q, const void *qd, con
                : launch_vjp_k<T, 64, MODE, false, false>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
 }
 
+template <typename T, int NMAX, int BLOCK, int MODE, int TRIG>
+int launch_vjp_dh_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                    const void *w, void *gq, void *gqd, void *gqdd, void *ws,
+                    const double *base18, cudaStream_t stream)
+{
+    double b[18];
+    rd_convert_base_dh(m, base18, b);
+    BaseParams<T> bp;
+    for (int k = 0; k < 6; ++k) {
+        bp.V0[k] = (T)b[k];
+        bp.dV0[k] = (T)b[6 + k];
+        bp.Fn[k] = (T)b[12 + k];
+    }
+    DhParamConsts<T, NMAX> pc;
+    for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (T)m->host_dh64[k];
+    for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = T(0);
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    rnea_vjp_dh_kernel<T, NMAX, BLOCK, MODE, TRIG><<<grid, BLOCK, 0, stream>>>(
+        pc, m->n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
+        static_cast<const T *>(qdd), static_cast<const T *>(w), static_cast<T *>(gq),
+        static_cast<T *>(gqd), static_cast<T *>(gqdd), static_cast<T *>(ws), bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_vjp common-normal kernel launch");
+    return RD_OK;
+}
+
+template <typename T, int MODE, int TRIG>
+int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                  const void *w, void *gq, void *gqd, void *gqdd, void *ws,
+                  const double *base18, cudaStream_t s)
+{
+    // small batches: 32-thread blocks spread the few warps over more SMs
+    const bool small = B <= 152 * 128;
+    if (m->n <= 32)
+        return small ? launch_vjp_dh_k<T, 32, 32, MODE, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s)
+                     : launch_vjp_dh_k<T, 32, 64, MODE, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
+    return small ? launch_vjp_dh_k<T, 128, 32, MODE, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s)
+                 : launch_vjp_dh_k<T, 128, 64, MODE, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
+}
+
+// Common-normal kernel for whole 16-byte chunks (n % 4 == 0, n <= 128, aligned
+// rows), unless the joint-frame kernel is asked for; else the joint-frame kernel.
+template <typename T, int MODE>
+int launch_vjp_any(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                   const void *w, void *gq, void *gqd, void *gqdd, void *ws,
+                   const double *base18, bool fast, bool joint_frames, cudaStream_t s)
+{
+    const bool dh = !joint_frames && m->n % 4 == 0 && m->n <= 128 && vjp_aligned16(q) &&
+                    vjp_aligned16(qd) && vjp_aligned16(qdd) && vjp_aligned16(w) &&
+                    vjp_aligned16(gq) && vjp_aligned16(gqd) && vjp_aligned16(gqdd);
+    if (dh) {
+        if (sizeof(T) == 4 && fast)
+            return launch_vjp_dh<T, MODE, kTrigSfu>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
+        return launch_vjp_dh<T, MODE, kTrigPoly>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
+    }
+    return launch_vjp_mode<T, MODE>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast, s);
+}
+
 template <typename T>
 int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                  const void *w, void *gq, void *gqd, void *gqdd, const double *base18, int mode,
                  void *ws, size_t ws_bytes, cudaStream_t s)
 {
     const bool fast = (mode & RD_FLAG_FAST_TRIG) != 0;
+    const bool joint_frames = (mode & RD_VJP_FLAG_JOINT_FRAMES) != 0;
     mode &= 0xff;
     const size_t need = (size_t)m->n * kVjpStateScalars * (size_t)B * sizeof(T);
     if (mode == RD_VJP_AUTO) {
@@ -93,11 +153,12 @@ int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
             return rd_fail(RD_ERR_ARG, "rnea_vjp: store mode needs a %zu-byte workspace (%zu given)",
                            need, ws_bytes);
         if (!vjp_aligned16(ws)) return rd_fail(RD_ERR_ARG, "rnea_vjp: workspace not 16-byte aligned");
-        return launch_vjp_mode<T, kVjpStore>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast, s);
+        return launch_vjp_any<T, kVjpStore>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast,
+                                            joint_frames, s);
     }
     if (mode == RD_VJP_RECOMPUTE)
-        return launch_vjp_mode<T, kVjpRecompute>(m, B, q, qd, qdd, w, gq, gqd, gqdd, nullptr, base18,
-                                                 fast, s);
+        return launch_vjp_any<T, kVjpRecompute>(m, B, q, qd, qdd, w, gq, gqd, gqdd, nullptr,
+                                                base18, fast, joint_frames, s);
     return rd_fail(RD_ERR_ARG, "rnea_vjp: unknown mode %d", mode);
 }
 
