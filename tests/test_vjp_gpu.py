@@ -136,3 +136,55 @@ def test_vjp_full_size_sampled(cuda_lib):
         idx = np.arange(0, B, 64)
         ref = oracle.rnea_grad(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd", "w")))
         assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+
+
+# ---- common-normal frames (rows with n % 4 == 0 and 16-byte alignment)
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("n", [4, 8, 12, 64, 100, 128])
+def test_vjp_common_normal_frames_match_complex_step(cuda_lib, n, dtype, mode):
+    g, ref, _, _ = run(cuda_lib, n, 150, dtype, mode, seed=13)
+    err = grad_err(g, ref)
+    assert err <= TOL[dtype], f"n={n} {dtype} mode={mode}: {err:.3e}"
+
+
+def test_vjp_common_normal_base_motion_and_wrench(cuda_lib):
+    """V_0, dV_0 and F_{n+1} converted into the recursion's frames on the host."""
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    for mode in (1, 2):
+        g, ref, _, _ = run(cuda_lib, 8, 50, "float64", mode, base=base)
+        assert grad_err(g, ref) <= TOL["float64"]
+
+
+def test_vjp_frames_agree_fp64(cuda_lib):
+    """The common-normal and joint-frame kernels give one gradient to rounding."""
+    flag = cuda_lib.RD_VJP_FLAG_JOINT_FRAMES
+    for mode in (1, 2):
+        a, _, _, _ = run(cuda_lib, 24, 200, "float64", mode, seed=6)
+        b, _, _, _ = run(cuda_lib, 24, 200, "float64", mode | flag, seed=6)
+        for x, y in zip(a, b):
+            assert np.max(np.abs(x - y)) <= 1e-10 * np.max(np.abs(x))
+
+
+def test_vjp_common_normal_fast_trig(cuda_lib):
+    g, ref, _, _ = run(cuda_lib, 32, 200, "float32", 2 | cuda_lib.RD_FLAG_FAST_TRIG, seed=17)
+    assert grad_err(g, ref) <= TOL["float32"]
+
+
+def test_vjp_recompute_large_batch_sampled(cuda_lib):
+    """n = 32, B = 262144 FP32 in recompute mode (the large-batch adjoint
+    workload): every 512th instance against the oracle's gradient."""
+    import torch
+
+    n, B = 32, 262144
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=101, kinds=("q", "qd", "qdd", "w"))
+    host = {k: st[k].astype(np.float32) for k in st}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    g = cuda_lib.rnea_vjp(cuda_lib.Model(ch), dev["q"], dev["qd"], dev["qdd"], dev["w"],
+                          mode=cuda_lib.RD_VJP_RECOMPUTE)
+    idx = np.arange(0, B, 512)
+    ref = oracle.rnea_grad(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd", "w")))
+    assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
