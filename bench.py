@@ -44,28 +44,31 @@ ROTATE = 8  # input sets cycled between steps; 8 x 33.5 MB > 2 x L2 (129 MB)
 # the measured time; the kernel's own count is reported beside it.
 ALGO_FLOP_PER_LINK = 470
 # Executed arithmetic of the joint-frame kernels per link (FMA = 2): rotation 18
-# + forward step 94 + bias wrench 102 + carry 60.
-JOINT_FRAME_FLOP_PER_LINK = 274
+# + forward step 94 + bias wrench 93 + carry 60.
+JOINT_FRAME_FLOP_PER_LINK = 265
 
 
 def dh_param_flops(n, K):
     """Executed arithmetic (FMA = 2) of one instance in the common-normal kernel
     with full state for links 0..K-1: a stored link costs sin/cos 26 + rotation
-    products 4 + forward step 86 + bias wrench 102 + backward carry 44 + products 4;
+    products 4 + forward step 86 + bias wrench 93 + backward carry 44 + products 4;
     a link without full state adds the re-derivation of its motion (86) and
     moves its bias wrench to the backward sweep; the top link adds instead of
     carrying (-38) and the lowest re-derived link needs no inverse step (-86)."""
-    stored, rederived = 266, 352
+    stored, rederived = 257, 343
     total = K * stored + (n - K) * rederived - 38
     if K < n:
         total -= 86
     return total
 
 
-# adjoint arithmetic per link (FMA = 2): sweep 1 155 (rotation, motion, wrench
-# adjoint), sweep 2 500 (bias wrench, carries, inertia products, ad terms,
-# gradients) plus 137 to re-derive the motion and wrench adjoint (recompute mode)
-VJP_FLOP_PER_LINK = {1: 655, 2: 792}
+# adjoint arithmetic per link of the common-normal kernel the bench runs (FMA = 2):
+# sweep 1 155 (sin/cos 26, rotation products 4, motion step 86, wrench-adjoint
+# step 39); sweep 2 466 (products 4, bias wrench 93, carry 44, three inertia
+# products 126, ad terms 30, seeds 42, two adjoint carries 88 and their coupling
+# 8, gradients 31); recompute mode adds 151 (sin/cos 26, inverse motion step 86,
+# inverse wrench-adjoint step 39)
+VJP_FLOP_PER_LINK = {1: 621, 2: 772}
 # algorithmic arithmetic of the adjoint per link: about three inverse-dynamics
 # passes of the general formulation above
 VJP_ALGO_FLOP_PER_LINK = 1400

@@ -86,7 +86,11 @@ enum rd_variant {
                                  for the rest, whose motion is re-derived; otherwise every link
                                  keeps its state in shared memory. AUTO takes this kernel for
                                  FP32 batches of more than 2048 whole-chunk rows. */
-    RD_VARIANT_SERIAL_DH_RECOMPUTE = 7 /* as 6 with K = 0 (no full state) */
+    RD_VARIANT_SERIAL_DH_RECOMPUTE = 7, /* as 6 with K = 0 (no full state) */
+    RD_VARIANT_SERIAL_DH_TMEM = 8 /* as 6 (FP32, n <= 32, n % 4 == 0, aligned rows) with the
+                                     state of the first 16 links in tensor memory: blocks of
+                                     128 threads, four per SM, each owning 128 TMEM columns;
+                                     K by RD_TUNE_STORED_LINKS (0 = largest that fits) */
 };
 /* Lane-parallel scan: L lanes of one warp per instance, L in {2,4,8,16,32};
  * each lane owns ceil(n/L) consecutive links, lanes combine their segments
@@ -383,12 +387,14 @@ int rd_joint_trig(int flags, const float *x, float *s, float *c, int count, void
  *                 RD_VARIANT_SERIAL_DH, ..._DH_RECOMPUTE with shared-memory
  *                 constants, RD_VARIANT_SCAN(L)) or RD_RNEA_KERNEL_DH_PARAM for
  *                 the common-normal kernel with its constants as a kernel
- *                 parameter;
+ *                 parameter, RD_RNEA_KERNEL_DH_TMEM for its variant with state in
+ *                 tensor memory;
  *   block         threads per block;
  *   stored_links  links whose full backward-sweep state the kernel keeps.
  * All 0 before the first launch on this thread. Errors: RD_ERR_ARG (null output).
  */
 #define RD_RNEA_KERNEL_DH_PARAM 0x206
+#define RD_RNEA_KERNEL_DH_TMEM 0x208
 int rd_rnea_last_config(int *kernel, int *block, int *stored_links);
 
 /* Message for the last error on the calling thread ("" if none). */

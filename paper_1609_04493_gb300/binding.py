@@ -20,6 +20,7 @@ RD_VARIANT_SERIAL_REGSTATE = 4
 RD_VARIANT_SERIAL_HYBRID = 5
 RD_VARIANT_SERIAL_DH = 6
 RD_VARIANT_SERIAL_DH_RECOMPUTE = 7
+RD_VARIANT_SERIAL_DH_TMEM = 8
 
 
 RD_FLAG_FAST_TRIG = 0x1000
@@ -151,6 +152,7 @@ def measure_fma_peak(dtype="float32", stream=None):
 
 
 RD_RNEA_KERNEL_DH_PARAM = 0x206
+RD_RNEA_KERNEL_DH_TMEM = 0x208
 
 
 def rnea_last_config():

@@ -56,10 +56,10 @@ int rd_build_dh(int n, const std::vector<double> &c64, std::vector<double> &dh64
                 double GBp[3], double *phi_last);
 int rd_rnea_dh_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
-                   int kfull, cudaStream_t s);
+                   int kfull, int tmem, cudaStream_t s);
 int rd_rnea_dh_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
-                   int kfull, cudaStream_t s);
+                   int kfull, int tmem, cudaStream_t s);
 int rd_rnea_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
                          const void *qdd, void *tau, const double *base18, int variant,
                          cudaStream_t s);

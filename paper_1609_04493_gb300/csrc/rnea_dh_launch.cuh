@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "rdyn_internal.h"
+#include "rnea_dht.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
@@ -205,6 +206,103 @@ int launch_dhp(const rd_model *m, int block, int K, int B, const void *q, const 
                : launch_dhp_b<T, 128, kTrigPoly>(m, block, K, B, q, qd, qdd, tau, base, smem, s);
 }
 
+// ---- TMEM-state kernel (FP32, n <= 32, n % 4 == 0, aligned rows)
+
+template <int TRIG, int STAGES>
+int launch_dht_k(const rd_model *m, int K, int TL, int B, const void *q, const void *qd,
+                 const void *qdd, void *tau, const BaseParams<float> &base, size_t smem,
+                 cudaStream_t stream)
+{
+    static std::atomic<uint64_t> configured{0};
+    auto kern = rnea_dht_kernel<32, TRIG, STAGES>;
+    const uint64_t bit = 1ull << (m->device & 63);
+    if (!(configured.load() & bit)) {
+        // the opt-in limit covers static and dynamic shared memory together
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     dh_smem_optin(m->device) - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+        configured.fetch_or(bit);
+    }
+    DhParamConsts<float, 32> pc;
+    for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (float)m->host_dh64[k];
+    for (int k = m->n * kDhConsts; k < 32 * kDhConsts; ++k) pc.c[k] = 0.0f;
+    // four blocks per SM, each with an equal share of the batch in rounds of
+    // at most 128 instances
+    static std::atomic<int> sms[64];
+    const int d = m->device & 63;
+    if (sms[d].load() == 0) sms[d].store(dh_device_attr(m->device, cudaDevAttrMultiProcessorCount, 1));
+    const long long max_grid = 4LL * sms[d].load(), min_grid = ((long long)B + 31) / 32;
+    const long long grid = max_grid < min_grid ? max_grid : min_grid;
+    const long long per_block = ((long long)B + grid - 1) / grid;
+    const long long rounds = (per_block + kDhtThreads - 1) / kDhtThreads;
+    const long long per_round = (per_block + rounds - 1) / rounds;
+    rd_note_rnea(RD_RNEA_KERNEL_DH_TMEM, kDhtThreads, K);
+    kern<<<(unsigned)grid, kDhtThreads, smem, stream>>>(pc, m->n, K, TL, B, (int)per_block,
+                                              (int)per_round, static_cast<const float *>(q),
+                                              static_cast<const float *>(qd),
+                                              static_cast<const float *>(qdd),
+                                              static_cast<float *>(tau), base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea TMEM-state kernel launch");
+    return RD_OK;
+}
+
+// Shared memory a block may use with four blocks per SM, and the padding that
+// keeps a fifth from fitting (each block holds 128 of the SM's 512 TMEM columns).
+inline void dht_smem_bounds(int device, size_t &max_block, size_t &min_block)
+{
+    static std::atomic<int> smem_sm[64];
+    const int d = device & 63;
+    if (smem_sm[d].load() == 0)
+        smem_sm[d].store(dh_device_attr(device, cudaDevAttrMaxSharedMemoryPerMultiprocessor, 0));
+    const size_t sm = (size_t)smem_sm[d].load();
+    const size_t reserve = 1024 + 16;  // per-block reserve and the static TMEM-address word
+    max_block = sm / 4 > reserve ? sm / 4 - reserve : 0;
+    min_block = sm / 5 + 16 > reserve ? ((sm / 5 + 16 - reserve) + 15) / 16 * 16 : 0;
+}
+
+// K < 0: the largest K whose state fits four blocks per SM (two-stage ring if
+// the three-stage one does not fit); K >= 0: that K with the deepest ring that fits.
+inline int launch_dht(const rd_model *m, int K, int B, const void *q, const void *qd,
+                      const void *qdd, void *tau, const BaseParams<float> &base, bool fast,
+                      cudaStream_t s)
+{
+    const int n = m->n;
+    size_t max_block, min_block;
+    dht_smem_bounds(m->device, max_block, min_block);
+    auto need = [&](int k, int stages) {
+        return dht_smem_per_thread(n, k, k < kDhtMaxTmemLinks ? k : kDhtMaxTmemLinks, stages) *
+               kDhtThreads;
+    };
+    int stages = 0;
+    if (K < 0) {
+        for (int k = n; k >= 0 && !stages; k -= 4)
+            for (int st = 3; st >= 2 && !stages; --st)
+                if (need(k, st) <= max_block) {
+                    K = k;
+                    stages = st;
+                }
+    } else {
+        K = K > n ? n : 4 * (K / 4);
+        for (int st = 3; st >= 2 && !stages; --st)
+            if (need(K, st) <= max_block) stages = st;
+    }
+    if (!stages)
+        return rd_fail(RD_ERR_ARG, "rnea_batch: TMEM-state kernel: state of %d links does not fit "
+                                   "four blocks per SM", K);
+    const int TL = K < kDhtMaxTmemLinks ? K : kDhtMaxTmemLinks;
+    size_t smem = need(K, stages);
+    if (smem < min_block) smem = min_block;
+    if (stages == 3)
+        return fast ? launch_dht_k<kTrigSfu, 3>(m, K, TL, B, q, qd, qdd, tau, base, smem, s)
+                    : launch_dht_k<kTrigPoly, 3>(m, K, TL, B, q, qd, qdd, tau, base, smem, s);
+    return fast ? launch_dht_k<kTrigSfu, 2>(m, K, TL, B, q, qd, qdd, tau, base, smem, s)
+                : launch_dht_k<kTrigPoly, 2>(m, K, TL, B, q, qd, qdd, tau, base, smem, s);
+}
+
 // stored: state for the first K links (kfull; < 0 = library default), else
 // none. Rows with n % 4 == 0, n <= 128 and 16-byte alignment take the
 // parameter-constant kernel; others the shared-memory-constant kernel, with
@@ -212,7 +310,7 @@ int launch_dhp(const rd_model *m, int block, int K, int B, const void *q, const 
 template <typename T>
 int dh_launch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
               void *tau, const double *base18, bool stored, int block, bool fast, int kfull,
-              cudaStream_t s)
+              bool tmem, cudaStream_t s)
 {
     double b[18];
     rd_convert_base_dh(m, base18, b);
@@ -221,6 +319,14 @@ int dh_launch(const rd_model *m, int B, const void *q, const void *qd, const voi
         base.V0[k] = (T)b[k];
         base.dV0[k] = (T)b[6 + k];
         base.Fn[k] = (T)b[12 + k];
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (tmem) {
+            if (!dhp_eligible<T>(m, q, qd, qdd, tau) || m->n > 32)
+                return rd_fail(RD_ERR_ARG, "rnea_batch: the TMEM-state kernel needs FP32, "
+                                           "n %% 4 == 0, n <= 32 and 16-byte aligned rows");
+            return launch_dht(m, stored ? kfull : 0, B, q, qd, qdd, tau, base, fast, s);
+        }
     }
     if (dhp_eligible<T>(m, q, qd, qdd, tau))
         return launch_dhp<T>(m, block ? block : 32, stored ? kfull : 0, B, q, qd, qdd, tau, base,

@@ -319,7 +319,7 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         // parameter, full state for the library's K (about 22% below the
         // joint-frame kernels at n = 16..100, B = 65536; see rnea_dh_launch.cuh)
         return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, 1, block, fast,
-                              reglinks ? reglinks : -1, s);
+                              reglinks ? reglinks : -1, 0, s);
     }
     if (variant == RD_VARIANT_AUTO) {
         // Sweep on GB300 at B = 65536 (modes x block sizes x stored links):
@@ -362,13 +362,15 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     }
     if (variant == RD_VARIANT_SERIAL_REGSTATE)
         return launch_regstate<T>(m, block, reglinks, B, q, qd, qdd, tau, base18, fast, s);
-    if (variant == RD_VARIANT_SERIAL_DH || variant == RD_VARIANT_SERIAL_DH_RECOMPUTE) {
-        const int stored = variant == RD_VARIANT_SERIAL_DH;
+    if (variant == RD_VARIANT_SERIAL_DH || variant == RD_VARIANT_SERIAL_DH_RECOMPUTE ||
+        variant == RD_VARIANT_SERIAL_DH_TMEM) {
+        const int stored = variant != RD_VARIANT_SERIAL_DH_RECOMPUTE;
+        const int tmem = variant == RD_VARIANT_SERIAL_DH_TMEM;
         const int kfull = reglinks ? reglinks : -1;
         if constexpr (sizeof(T) == 4)
-            return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, s);
+            return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, tmem, s);
         else
-            return rd_rnea_dh_f64(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, s);
+            return rd_rnea_dh_f64(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, tmem, s);
     }
     if (variant == RD_VARIANT_SERIAL_HYBRID) {
         if (!block) block = 32;

@@ -253,15 +253,14 @@ __device__ __forceinline__ Wrench<T> carry_wrench_R(const Rot<T> &R, V3<T> b,
 
 // Bias wrench F_hat = J dV - ad^T_V (J V) (Sec. III-C), written with the
 // centre of mass c:
-//   a_c = a + w x v + al x c + w x (w x c),   f = m a_c,
-//   n   = c x f + I_c al + w x (I_c w).
+//   a_c = a + w x v + al x c + w x (w x c) = a + al x c + w x (v + w x c),
+//   f = m a_c,   n = c x f + I_c al + w x (I_c w).
 template <typename T>
 __device__ __forceinline__ Wrench<T> bias_wrench(T m, V3<T> c, const T *I, const Motion<T> &x)
 {
-    V3<T> wc = cross3(x.w, c);
-    V3<T> ac = cross_add(x.w, x.v, x.a);
-    ac = cross_add(x.al, c, ac);
-    ac = cross_add(x.w, wc, ac);
+    const V3<T> vc = cross_add(x.w, c, x.v);  // velocity of the centre of mass
+    V3<T> ac = cross_add(x.al, c, x.a);
+    ac = cross_add(x.w, vc, ac);
     Wrench<T> F;
     F.f = scale3(m, ac);
     V3<T> Iw = sym_mul(I, x.w);

@@ -232,3 +232,71 @@ def test_dh_rejects_state_beyond_shared_memory(cuda_lib):
          | cuda_lib.RD_TUNE_BLOCK(128))
     with pytest.raises(cuda_lib.RdError, match="shared"):
         cuda_lib.rnea(model, z, z, z, variant=v)
+
+
+# ---- state of the first 16 links in tensor memory (RD_VARIANT_SERIAL_DH_TMEM)
+
+@pytest.mark.parametrize("n", [4, 8, 12, 16, 20, 24, 28, 32])
+def test_tmem_state_parity(cuda_lib, n):
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    tau, ref = run(cuda_lib, ch, 1000, "float32", cuda_lib.RD_VARIANT_SERIAL_DH_TMEM)
+    err = oracle.rel_err(tau, ref)
+    assert err <= TOL["float32"], f"n={n}: rel err {err:.3e}"
+
+
+@pytest.mark.parametrize("K", [4, 8, 16, 20, 24])
+def test_tmem_state_split_points(cuda_lib, K):
+    """K links with full state: the first min(K, 16) in TMEM, the rest in shared
+    memory, cos/sin only beyond K."""
+    ch = chaingen.make_chain(32)
+    v = cuda_lib.RD_VARIANT_SERIAL_DH_TMEM | cuda_lib.RD_TUNE_STORED_LINKS(K)
+    tau, ref = run(cuda_lib, ch, 777, "float32", v)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
+@pytest.mark.parametrize("B", [1, 127, 129, 4097])
+def test_tmem_state_ragged_batches(cuda_lib, B):
+    """Threads past the batch run the last row and store nothing."""
+    ch = chaingen.make_chain(32)
+    tau, ref = run(cuda_lib, ch, B, "float32", cuda_lib.RD_VARIANT_SERIAL_DH_TMEM)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
+def test_tmem_state_base_and_fast_trig(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25,
+                     0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    ch = chaingen.make_chain(16)
+    tau, ref = run(cuda_lib, ch, 500, "float32", cuda_lib.RD_VARIANT_SERIAL_DH_TMEM, base=base)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+    v = cuda_lib.RD_VARIANT_SERIAL_DH_TMEM | cuda_lib.RD_FLAG_FAST_TRIG
+    tau, ref = run(cuda_lib, ch, 500, "float32", v)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
+def test_tmem_state_full_batch_sampled(cuda_lib):
+    """n = 32, B = 65536: every instance of the batch in one wave; every 16th
+    instance against the oracle, and back-to-back launches agree bit for bit."""
+    torch = _torch()
+    n, B = 32, 65536
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=31)
+    host = {k: st[k].astype(np.float32) for k in ("q", "qd", "qdd")}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    model = cuda_lib.Model(ch)
+    v = cuda_lib.RD_VARIANT_SERIAL_DH_TMEM
+    t1 = cuda_lib.rnea(model, dev["q"], dev["qd"], dev["qdd"], variant=v)
+    t2 = cuda_lib.rnea(model, dev["q"], dev["qd"], dev["qdd"], variant=v)
+    torch.cuda.synchronize()
+    assert torch.equal(t1, t2)
+    idx = np.arange(0, B, 16)
+    ref = oracle.rnea(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd")))
+    assert oracle.rel_err(t1.cpu().numpy()[idx], ref) <= TOL["float32"]
+
+
+def test_tmem_state_rejects_unsupported_rows(cuda_lib):
+    torch = _torch()
+    model = cuda_lib.Model(chaingen.make_chain(36))
+    z = torch.zeros((64, 36), dtype=torch.float32, device="cuda")
+    with pytest.raises(cuda_lib.RdError, match="TMEM"):
+        cuda_lib.rnea(model, z, z, z, variant=cuda_lib.RD_VARIANT_SERIAL_DH_TMEM)
