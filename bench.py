@@ -72,6 +72,15 @@ VJP_FLOP_PER_LINK = {1: 621, 2: 772}
 # algorithmic arithmetic of the adjoint per link: about three inverse-dynamics
 # passes of the general formulation above
 VJP_ALGO_FLOP_PER_LINK = 1400
+# forward dynamics per link (articulated-body algorithm), FMA = 2: ~720 FP32
+# flop (bias motion and wrenches, backward wrench carry, z_hat / lambda
+# transforms) and ~800 FP64 flop (articulated-inertia congruence, the rank-one
+# update and the Omega solves), the split of the design's precision plan
+FD_FLOP32_PER_LINK = 720
+FD_FLOP64_PER_LINK = 800
+# bytes an inverse-dynamics link of the uneven workload moves: q, qd, qdd, tau
+# (16) plus its robot's constants streamed per request (112)
+UNEVEN_ID_BYTES_PER_LINK = 128
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
@@ -214,6 +223,15 @@ def kernel_sources_hash(files=RNEA_KERNEL_SOURCES):
     return hs.hexdigest()[:16]
 
 
+def fp32_peak_tflops():
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+
+
+def fd_algorithmic_seconds_per_link():
+    return (FD_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
+            + FD_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -330,10 +348,15 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
             rd.aba(model, *x, workspace=ws, out=o)
 
         t = time_calls(torch, call, steps, 3, dist, sampler)
+        t_alg = B * n * fd_algorithmic_seconds_per_link()
         out[f"n{n}_B{B}"] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
-                             "steps": steps}
+                             "steps": steps, "roofline_ms": t_alg * 1e3,
+                             "roofline_frac": t_alg / (t / steps)}
     out["metric"] = ("forward dynamics (articulated-body, FP32 data, FP64 inertia updates and "
                      "solves) evals/s")
+    out["roofline"] = (f"combined FP32 + FP64 time of {FD_FLOP32_PER_LINK} FP32 and "
+                       f"{FD_FLOP64_PER_LINK} FP64 algorithmic flop per link at the derived FP32 "
+                       f"and nominal FP64 peaks, divided by the measured time")
     return out
 
 
@@ -361,6 +384,18 @@ def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
         res[name] = {"value": count * steps / t, "unit": "requests/s",
                      "ms_per_step": t / steps * 1e3, "steps": steps,
                      "schedule": sc, "tune": tu}
+    n_fd = int(np.sum(np.where(kinds == 1, plan.lengths, 0)))
+    n_id = J - n_fd
+    t_alg = (n_id * max(ALGO_FLOP_PER_LINK / (fp32_peak_tflops() * 1e12),
+                        UNEVEN_ID_BYTES_PER_LINK / (measured_peaks().get("hbm_gbs", 6800.0) * 1e9))
+             + n_fd * fd_algorithmic_seconds_per_link())
+    for name in ("persistent_tuned", "per_group_launches"):
+        res[name]["roofline_frac"] = t_alg / (res[name]["ms_per_step"] * 1e-3)
+    res["roofline_ms"] = t_alg * 1e3
+    res["roofline"] = (f"inverse dynamics links at the larger of {ALGO_FLOP_PER_LINK} flop / FP32 "
+                       f"peak and {UNEVEN_ID_BYTES_PER_LINK} B (joint values, torque, streamed "
+                       f"constants) / measured HBM bandwidth, plus forward dynamics links at the "
+                       f"combined FP32 + FP64 time; divided by the measured time")
     res["workload"] = (f"{count} requests, own robot each, n uniform in 6..100 "
                        f"({J} joints), {int(kinds.sum())} forward / {count - int(kinds.sum())} "
                        f"inverse dynamics, FP32 (FP64 inertia updates and solves)")
