@@ -78,6 +78,13 @@ VJP_ALGO_FLOP_PER_LINK = 1400
 # update and the Omega solves), the split of the design's precision plan
 FD_FLOP32_PER_LINK = 720
 FD_FLOP64_PER_LINK = 800
+# executed arithmetic of the common-normal forward-dynamics kernel per link:
+# FP32 257 (sin/cos 26, products 4, bias motion 86, bias wrench 93, wrench carry
+# 44, products 4); FP64 400 (projected inertia 35, two plane rotations and the
+# shift of the articulated-inertia update 235, z_hat carry 60, Omega solve 12,
+# lambda step 56)
+FD_EXEC_FLOP32_PER_LINK = 257
+FD_EXEC_FLOP64_PER_LINK = 400
 # bytes an inverse-dynamics link of the uneven workload moves: q, qd, qdd, tau
 # (16) plus its robot's constants streamed per request (112)
 UNEVEN_ID_BYTES_PER_LINK = 128
@@ -349,14 +356,19 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
 
         t = time_calls(torch, call, steps, 3, dist, sampler)
         t_alg = B * n * fd_algorithmic_seconds_per_link()
+        t_exec = B * n * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
+                          + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
         out[f"n{n}_B{B}"] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
                              "steps": steps, "roofline_ms": t_alg * 1e3,
-                             "roofline_frac": t_alg / (t / steps)}
+                             "roofline_frac": t_alg / (t / steps),
+                             "executed_roofline_frac": t_exec / (t / steps)}
     out["metric"] = ("forward dynamics (articulated-body, FP32 data, FP64 inertia updates and "
                      "solves) evals/s")
     out["roofline"] = (f"combined FP32 + FP64 time of {FD_FLOP32_PER_LINK} FP32 and "
                        f"{FD_FLOP64_PER_LINK} FP64 algorithmic flop per link at the derived FP32 "
-                       f"and nominal FP64 peaks, divided by the measured time")
+                       f"and nominal FP64 peaks, divided by the measured time; executed: the "
+                       f"kernel's own {FD_EXEC_FLOP32_PER_LINK} FP32 and "
+                       f"{FD_EXEC_FLOP64_PER_LINK} FP64 flop per link")
     return out
 
 

@@ -58,6 +58,9 @@ enum rd_status {
  * (FP32 for RD_F32) instead of the default FP64; the articulated-inertia update
  * and the Omega solves stay in FP64 either way. */
 #define RD_ABA_SCANS_IN_DTYPE 0x1
+/* aba_batch flag: run the joint-frame kernel even where the common-normal one
+ * applies (n % 4 == 0, n <= 64, 16-byte aligned rows), for comparisons. */
+#define RD_ABA_JOINT_FRAMES 0x2
 
 /* Per-instance status word of aba_batch (0 = fine). */
 #define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */

@@ -377,6 +377,7 @@ def rnea_autograd(model, q, qd, qdd, base=None, vjp_mode=RD_VJP_RECOMPUTE):
 
 
 RD_ABA_SCANS_IN_DTYPE = 0x1
+RD_ABA_JOINT_FRAMES = 0x2
 
 
 def aba_workspace_bytes(model, B, dtype_code, flags=0):

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "aba.cuh"
+#include "aba_dh.cuh"
 #include "rdyn_internal.h"
 
 namespace rdyn {
@@ -60,6 +61,45 @@ int launch_aba_k(const rd_model *m, int B, const void *q, const void *qd, const 
     return RD_OK;
 }
 
+template <typename T, typename Z, int NMAX, int TRIG>
+int launch_aba_dh_k(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                    void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
+{
+    constexpr int BLOCK = 64;
+    const int n = m->n;
+    double bb[18];
+    rd_convert_base_dh(m, base18, bb);
+    BaseParams<T> bp;
+    for (int k = 0; k < 6; ++k) {
+        bp.V0[k] = (T)bb[k];
+        bp.dV0[k] = (T)bb[6 + k];
+        bp.Fn[k] = (T)bb[12 + k];
+    }
+    AbaDhConsts<T, NMAX> pc;
+    for (int k = 0; k < NMAX * kDhConsts; ++k)
+        pc.c[k] = k < n * kDhConsts ? (T)m->host_dh64[k] : T(0);
+    for (int k = 0; k < NMAX * kAbaDh64; ++k)
+        pc.d[k] = k < n * kAbaDh64 ? m->host_aba64[k] : 0.0;
+    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
+    Z *wsz = reinterpret_cast<Z *>(static_cast<char *>(ws) + ((a + 255) & ~(size_t)255));
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    aba_dh_kernel<T, Z, NMAX, BLOCK, TRIG><<<grid, BLOCK, 0, stream>>>(
+        pc, n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
+        static_cast<const T *>(tau), static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz, bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "aba common-normal kernel launch");
+    return RD_OK;
+}
+
+template <typename T, typename Z>
+int launch_aba_dh(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                  void *qdd, int *status, void *ws, const double *base18, cudaStream_t s)
+{
+    if (m->n <= 32)
+        return launch_aba_dh_k<T, Z, 32, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    return launch_aba_dh_k<T, Z, 64, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+}
+
 template <typename T>
 int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                  void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
@@ -73,6 +113,14 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
     if (!aba_aligned16(ws)) return rd_fail(RD_ERR_ARG, "aba_batch: workspace not 16-byte aligned");
     const bool vec = m->n % 4 == 0 && aba_aligned16(q) && aba_aligned16(qd) &&
                      aba_aligned16(tau) && aba_aligned16(qdd);
+    if (vec && m->n <= 64 && !(flags & RD_ABA_JOINT_FRAMES)) {
+        // common-normal frames, constants as a kernel parameter (aba_dh.cuh)
+        if constexpr (sizeof(T) == 4) {
+            if (fp32_scans)
+                return launch_aba_dh<T, T>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+        }
+        return launch_aba_dh<T, double>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    }
     if constexpr (sizeof(T) == 4) {
         if (fp32_scans)
             return vec ? launch_aba_k<T, T, 64, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)

@@ -38,6 +38,20 @@ __device__ __forceinline__ void dh_trig(T x, T *s, T *c)
     else sincos_poly(x, s, c);
 }
 
+// Four joint values of a row (16-byte aligned) into registers.
+template <typename T>
+__device__ __forceinline__ void ld_row_chunk(const T *__restrict__ p, int i0, Chunk<T> &c)
+{
+    if constexpr (sizeof(T) == 4) {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p + i0));
+        c.v[0] = t.x; c.v[1] = t.y; c.v[2] = t.z; c.v[3] = t.w;
+    } else {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(p + i0));
+        double2 b = __ldg(reinterpret_cast<const double2 *>(p + i0 + 2));
+        c.v[0] = a.x; c.v[1] = a.y; c.v[2] = b.x; c.v[3] = b.y;
+    }
+}
+
 // The backward sweep needs qd and qdd only; they sit at positions 1 and 2 of
 // the forward ring's slots.
 template <typename T, int BLOCK>

@@ -17,19 +17,6 @@
 
 namespace rdyn {
 
-template <typename T>
-__device__ __forceinline__ void ld_row_chunk(const T *__restrict__ p, int i0, Chunk<T> &c)
-{
-    if constexpr (sizeof(T) == 4) {
-        float4 t = __ldg(reinterpret_cast<const float4 *>(p + i0));
-        c.v[0] = t.x; c.v[1] = t.y; c.v[2] = t.z; c.v[3] = t.w;
-    } else {
-        double2 a = __ldg(reinterpret_cast<const double2 *>(p + i0));
-        double2 b = __ldg(reinterpret_cast<const double2 *>(p + i0 + 2));
-        c.v[0] = a.x; c.v[1] = a.y; c.v[2] = b.x; c.v[3] = b.y;
-    }
-}
-
 // Fb_i = Ad_{f^-1} Fb_{i-1} + S w  (the velocity step without the ad term)
 template <typename T>
 __device__ __forceinline__ void fb_forward_dh(const DhRot<T> &R, V3<T> b, T w, V3<T> &fv,

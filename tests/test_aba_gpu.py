@@ -136,3 +136,44 @@ def test_aba_fp32_scans_flag(cuda_lib, n):
     idx = np.arange(0, B, max(1, B // 512))
     ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
     assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
+
+
+# ---- common-normal frames (n % 4 == 0, n <= 64, aligned rows)
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("n", [4, 8, 12, 32, 48])
+def test_aba_common_normal_frames_match_oracle(cuda_lib, n, dtype):
+    qdd, ch, h, _ = run(cuda_lib, n, 300, dtype, seed=41)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    assert oracle.rel_err(qdd, ref) <= TOL[dtype], f"n={n} {dtype}"
+
+
+def test_aba_common_normal_base_motion_and_wrench(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    qdd, ch, h, _ = run(cuda_lib, 12, 90, "float64", base=base)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=base)
+    assert oracle.rel_err(qdd, ref) <= TOL["float64"]
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_aba_frames_agree_fp64(cuda_lib, n):
+    """Common-normal and joint-frame kernels, one FP64 result to rounding."""
+    a, _, _, _ = run(cuda_lib, n, 200, "float64", seed=43)
+    b, _, _, _ = run(cuda_lib, n, 200, "float64", seed=43, flags=cuda_lib.RD_ABA_JOINT_FRAMES)
+    assert oracle.rel_err(a, b) <= 1e-9
+
+
+def test_aba_common_normal_flags_a_singular_joint(cuda_lib):
+    """Last link a point mass on its own axis: Omega_n = 0 is reported."""
+    import torch
+
+    ch = chaingen.make_chain(4, seed=5)
+    # last joint about z through its frame's origin, centre of mass exactly on it
+    ch.S[3] = [0.0, 0.0, 0.0, 0.0, 0.0, 1.0]
+    ch.inertia[3] = [1.0, 0.0, 0.0, 0.2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    model = cuda_lib.Model(ch)
+    x = torch.zeros((6, 4), dtype=torch.float64, device="cuda")
+    status = torch.full((6,), -7, dtype=torch.int32, device="cuda")
+    cuda_lib.aba(model, x, x, x + 1.0, status=status)
+    assert torch.all(status == 1)
