@@ -135,20 +135,18 @@ __device__ __forceinline__ Abi aba_dh_update(const Abi &P, double c, double s, c
     return o;
 }
 
-template <typename T, typename Z, int NMAX, int BLOCK, int TRIG>
-__global__ void __launch_bounds__(BLOCK)
-aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
-              const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
-              T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
-              Z *__restrict__ wsz, BaseParams<T> base)
+// One forward-dynamics instance in common-normal frames. sc: the chain's 16
+// constants per link in T; sd: its FP64 records; qr, qdr, taur, qddr: its joint
+// rows (VEC: n % 4 == 0 and 16-byte aligned, else element loads); ws / wsz and
+// (B, b): its workspace (aba_put). Returns 1 when an Omega_i <= 0 or a
+// non-finite qdd appeared.
+template <typename T, typename Z, int TRIG, bool VEC>
+__device__ __forceinline__ int aba_dh_instance(const T *sc, const double *sd, int n,
+                                               const T *__restrict__ qr, const T *__restrict__ qdr,
+                                               const T *__restrict__ taur, T *__restrict__ qddr,
+                                               T *__restrict__ ws, Z *__restrict__ wsz, int B, int b,
+                                               const BaseParams<T> &base)
 {
-    const T *sc = pc.c;
-    const double *sd = pc.d;
-    const int b = blockIdx.x * BLOCK + threadIdx.x;
-    if (b >= B) return;
-    const size_t row = (size_t)b * (size_t)n;
-    const T *qr = q + row, *qdr = qd + row, *taur = tau + row;
-    T *qddr = qdd_out + row;
     int bad = 0;
 
     // ---- sweep 1: bias motion (qdd = 0) and bias wrenches
@@ -157,26 +155,26 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
     x.w = mk3(base.V0[3], base.V0[4], base.V0[5]);
     x.a = mk3(base.dV0[0], base.dV0[1], base.dV0[2]);
     x.al = mk3(base.dV0[3], base.dV0[4], base.dV0[5]);
-    const int nchunks = n / 4;
+    const int nchunks = (n + 3) / 4;
     for (int kc = 0; kc < nchunks; ++kc) {
         const int i0 = 4 * kc;
-        Chunk<T> cq, cqd;
-        ld_row_chunk(qr, i0, cq);
-        ld_row_chunk(qdr, i0, cqd);
+        const Chunk<T> cq = ld_chunk<T, VEC>(qr, i0, n), cqd = ld_chunk<T, VEC>(qdr, i0, n);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = i0 + j;
-            DhLink<T> L;
-            load_dh(sc + i * kDhConsts, L);
-            T s, c;
-            dh_trig<T, TRIG>(cq.v[j] + L.th0, &s, &c);
-            x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, cqd.v[j], T(0), x);
-            const Wrench<T> Fh = bias_wrench(L.m, L.c, L.I, x);
-            const T vals[6] = {Fh.f.x, Fh.f.y, Fh.f.z, Fh.n.x, Fh.n.y, Fh.n.z};
+            if (VEC || i < n) {
+                DhLink<T> L;
+                load_dh(sc + i * kDhConsts, L);
+                T s, c;
+                dh_trig<T, TRIG>(cq.v[j] + L.th0, &s, &c);
+                x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, cqd.v[j], T(0), x);
+                const Wrench<T> Fh = bias_wrench(L.m, L.c, L.I, x);
+                const T vals[6] = {Fh.f.x, Fh.f.y, Fh.f.z, Fh.n.x, Fh.n.y, Fh.n.z};
 #pragma unroll
-            for (int k = 0; k < 6; ++k) aba_put(ws, B, b, i, k, vals[k]);
-            aba_put(ws, B, b, i, 8, c);
-            aba_put(ws, B, b, i, 9, s);
+                for (int k = 0; k < 6; ++k) aba_put(ws, B, b, i, k, vals[k]);
+                aba_put(ws, B, b, i, 8, c);
+                aba_put(ws, B, b, i, 9, s);
+            }
         }
     }
 
@@ -193,12 +191,12 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
     DhRot<Z> RnZ = dh_rot(Z(1), Z(0), Z(1), Z(0));
     V3<Z> bnZ = mk3(Z(0), Z(0), Z(0));
     double cn = 1.0, sn = 0.0;  // cos, sin of link i+1 in FP64
-    for (int i0 = n - 4; i0 >= 0; i0 -= 4) {
-        Chunk<T> ct;
-        ld_row_chunk(taur, i0, ct);
+    for (int i0 = ((n - 1) / 4) * 4; i0 >= 0; i0 -= 4) {
+        const Chunk<T> ct = ld_chunk<T, VEC>(taur, i0, n);
 #pragma unroll
         for (int j = 3; j >= 0; --j) {
             const int i = i0 + j;
+            if (!(VEC || i < n)) continue;
             Wrench<T> Fh;
             Fh.f = mk3(aba_get(ws, B, b, i, 0), aba_get(ws, B, b, i, 1), aba_get(ws, B, b, i, 2));
             Fh.n = mk3(aba_get(ws, B, b, i, 3), aba_get(ws, B, b, i, 4), aba_get(ws, B, b, i, 5));
@@ -274,34 +272,52 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int i = i0 + j;
-            const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
-            DhRot<Z> R;
-            V3<Z> bi;
-            if constexpr (sizeof(Z) == 8) {
-                const double *ri = sd + i * kAbaDh64;
-                R = dh_rot(ri[0], ri[1], (double)c, (double)s);
-                bi = mk3(ri[2], ri[3], ri[4]);
-            } else {
-                const T *Lt = sc + i * kDhConsts;
-                R = dh_rot((Z)Lt[0], (Z)Lt[1], (Z)c, (Z)s);
-                bi = mk3((Z)Lt[2], (Z)Lt[3], (Z)Lt[4]);
+            out.v[j] = T(0);
+            if (VEC || i < n) {
+                const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
+                DhRot<Z> R;
+                V3<Z> bi;
+                if constexpr (sizeof(Z) == 8) {
+                    const double *ri = sd + i * kAbaDh64;
+                    R = dh_rot(ri[0], ri[1], (double)c, (double)s);
+                    bi = mk3(ri[2], ri[3], ri[4]);
+                } else {
+                    const T *Lt = sc + i * kDhConsts;
+                    R = dh_rot((Z)Lt[0], (Z)Lt[1], (Z)c, (Z)s);
+                    bi = mk3((Z)Lt[2], (Z)Lt[3], (Z)Lt[4]);
+                }
+                // a = Ad_{f^-1} lambda
+                V3<Z> av = dh_mulT(R, cross_add(lw, bi, lv)), aw = dh_mulT(R, lw);
+                const V3<Z> uv = mk3(aba_zget(wsz, B, b, i, 0), aba_zget(wsz, B, b, i, 1), aba_zget(wsz, B, b, i, 2));
+                const V3<Z> uw = mk3(aba_zget(wsz, B, b, i, 3), aba_zget(wsz, B, b, i, 4), aba_zget(wsz, B, b, i, 5));
+                const Z ch = aba_zget(wsz, B, b, i, 6), iom = aba_zget(wsz, B, b, i, 7);
+                const double ua = (double)uv.x * av.x + (double)uv.y * av.y + (double)uv.z * av.z +
+                                  (double)uw.x * aw.x + (double)uw.y * aw.y + (double)uw.z * aw.z;
+                const double qdd_i = (double)ch - (double)iom * ua;
+                aw.z += (Z)qdd_i;
+                lv = av;
+                lw = aw;
+                out.v[j] = (T)qdd_i;
+                if (!(qdd_i == qdd_i)) bad = 1;
             }
-            // a = Ad_{f^-1} lambda
-            V3<Z> av = dh_mulT(R, cross_add(lw, bi, lv)), aw = dh_mulT(R, lw);
-            const V3<Z> uv = mk3(aba_zget(wsz, B, b, i, 0), aba_zget(wsz, B, b, i, 1), aba_zget(wsz, B, b, i, 2));
-            const V3<Z> uw = mk3(aba_zget(wsz, B, b, i, 3), aba_zget(wsz, B, b, i, 4), aba_zget(wsz, B, b, i, 5));
-            const Z ch = aba_zget(wsz, B, b, i, 6), iom = aba_zget(wsz, B, b, i, 7);
-            const double ua = (double)uv.x * av.x + (double)uv.y * av.y + (double)uv.z * av.z +
-                              (double)uw.x * aw.x + (double)uw.y * aw.y + (double)uw.z * aw.z;
-            const double qdd_i = (double)ch - (double)iom * ua;
-            aw.z += (Z)qdd_i;
-            lv = av;
-            lw = aw;
-            out.v[j] = (T)qdd_i;
-            if (!(qdd_i == qdd_i)) bad = 1;
         }
-        st_chunk<T, true>(qddr, i0, n, out);
+        st_chunk<T, VEC>(qddr, i0, n, out);
     }
+    return bad;
+}
+
+template <typename T, typename Z, int NMAX, int BLOCK, int TRIG>
+__global__ void __launch_bounds__(BLOCK)
+aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
+              const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
+              T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
+              Z *__restrict__ wsz, BaseParams<T> base)
+{
+    const int b = blockIdx.x * BLOCK + threadIdx.x;
+    if (b >= B) return;
+    const size_t row = (size_t)b * (size_t)n;
+    const int bad = aba_dh_instance<T, Z, TRIG, true>(pc.c, pc.d, n, q + row, qd + row, tau + row,
+                                                      qdd_out + row, ws, wsz, B, b, base);
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }
 

@@ -7,8 +7,9 @@
 // sit at [off_r, off_r + n_r) of every data array. One thread evaluates one
 // request with the per-instance bodies of the single-chain kernels (the
 // re-derive-in-the-backward-sweep RNEA, and the articulated-body algorithm
-// with FP64 inertia updates and solves), reading its robot's constants from
-// global memory since no two requests need share them.
+// with FP64 inertia updates and solves) in the common-normal frames of
+// spatial_dh.cuh, reading its robot's constants from global memory since no
+// two requests need share them.
 //
 // Scheduling: the host sorts requests (forward dynamics first, then by
 // decreasing n) so that the 32 requests a warp takes are alike.
@@ -19,18 +20,19 @@
 //   per-group:  one ordinary launch per run of equal (kind, n) in the sorted
 //               order -- the "one launch per request size" comparison.
 #pragma once
-#include "aba.cuh"
-#include "rnea_serial.cuh"
+#include "aba_dh.cuh"
+#include "rnea_dhp.cuh"
 
 namespace rdyn {
 
 template <typename T>
 struct FleetArgs {
-    const T *consts;          // [total links][24]
-    const double *consts64;   // [total links][24]
+    const T *consts;          // [total links][16] common-normal constants
+    const double *consts64;   // [total links][32] FP64 forward-dynamics records
     const int *robot_n;       // [robots]
     const int *robot_link;    // [robots] first constant row
-    const T *robot_tn;        // [robots][12] joint frame of the last link: R (9), r (3)
+    const T *robot_gb;        // [robots][12] base frame D_{-1} in frame 0: R (9), p (3)
+    const T *robot_tn;        // [robots][12] frame D_{n-1} in frame n: R (9), r (3)
     const int *order;         // [R] sorted request indices
     const int *req_robot;     // [R]
     const int *req_kind;      // [R] 0 = inverse, 1 = forward dynamics
@@ -42,18 +44,18 @@ struct FleetArgs {
     int *status;              // [R] or null
     unsigned char *ws;
     int *counter;
-    BaseParams<T> base;       // F_{n+1} in the frame of each robot's last link
+    BaseParams<T> base;       // V_0, dV_0 in frame 0; F_{n+1} in frame n
 };
 
-// Inverse dynamics of one instance, backward sweep re-deriving the motion
-// (rnea_serial_kernel<kRecompute> without the block-level staging).
-template <typename T>
-__device__ __forceinline__ void rnea_instance_recompute(const T *__restrict__ sc, int n,
-                                                        const T *__restrict__ qr,
-                                                        const T *__restrict__ qdr,
-                                                        const T *__restrict__ qddr,
-                                                        T *__restrict__ taur,
-                                                        const BaseParams<T> &base)
+// Inverse dynamics of one instance in common-normal frames, backward sweep
+// re-deriving the motion (the stateless rnea_dhp_kernel without staging; rows
+// of any length and alignment, constants read from global memory).
+template <typename T, int TRIG>
+__device__ __forceinline__ void rnea_dh_instance(const T *__restrict__ sc, int n,
+                                                 const T *__restrict__ qr,
+                                                 const T *__restrict__ qdr,
+                                                 const T *__restrict__ qddr, T *__restrict__ taur,
+                                                 const BaseParams<T> &base)
 {
     Motion<T> x;
     x.v = mk3(base.V0[0], base.V0[1], base.V0[2]);
@@ -61,36 +63,34 @@ __device__ __forceinline__ void rnea_instance_recompute(const T *__restrict__ sc
     x.a = mk3(base.dV0[0], base.dV0[1], base.dV0[2]);
     x.al = mk3(base.dV0[3], base.dV0[4], base.dV0[5]);
     for (int i = 0; i < n; ++i) {
-        LinkXf<T> X;
-        load_xf(sc + i * kLinkConsts, X);
+        DhXf<T> X;
+        load_dh_xf(sc + i * kDhConsts, X);
         T s, c;
-        sincos_t(__ldg(qr + i), &s, &c);
-        const Rot<T> R = make_rot(X.A, c, s);
-        x = forward_step_R(R, mk3(X.b[0], X.b[1], X.b[2]), __ldg(qdr + i), __ldg(qddr + i), x);
+        dh_trig<T, TRIG>(__ldg(qr + i) + X.th0, &s, &c);
+        x = dh_forward(dh_rot(X.ca, X.sa, c, s), X.b, __ldg(qdr + i), __ldg(qddr + i), x);
     }
     Wrench<T> F;
     F.f = mk3(base.Fn[0], base.Fn[1], base.Fn[2]);
     F.n = mk3(base.Fn[3], base.Fn[4], base.Fn[5]);
-    Rot<T> Rn;
+    DhRot<T> Rn = dh_rot(T(1), T(0), T(1), T(0));
     V3<T> bn = mk3(T(0), T(0), T(0));
     for (int i = n - 1; i >= 0; --i) {
-        LinkC<T> L;
-        load_link(sc + i * kLinkConsts, L);
+        DhLink<T> L;
+        load_dh(sc + i * kDhConsts, L);
         T s, c;
-        sincos_t(__ldg(qr + i), &s, &c);
-        const Rot<T> R = make_rot(L.A, c, s);
-        const V3<T> bi = mk3(L.b[0], L.b[1], L.b[2]);
-        const Wrench<T> Fh = bias_wrench(L.m, mk3(L.c[0], L.c[1], L.c[2]), L.I, x);
+        dh_trig<T, TRIG>(__ldg(qr + i) + L.th0, &s, &c);
+        const DhRot<T> R = dh_rot(L.ca, L.sa, c, s);
+        const Wrench<T> Fh = bias_wrench(L.m, L.c, L.I, x);
         if (i == n - 1) {
             F.f = add3(F.f, Fh.f);
             F.n = add3(F.n, Fh.n);
         } else {
-            F = carry_wrench_R(Rn, bn, F, Fh);
+            F = dh_carry(Rn, bn, F, Fh);
         }
         taur[i] = F.n.z;
-        if (i > 0) x = backward_recover_R(R, bi, __ldg(qdr + i), __ldg(qddr + i), x);
+        if (i > 0) x = dh_recover(R, L.b, __ldg(qdr + i), __ldg(qddr + i), x);
         Rn = R;
-        bn = bi;
+        bn = L.b;
     }
 }
 
@@ -101,9 +101,23 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int r)
     const int n = a.robot_n[robot];
     const long long lo = a.robot_link[robot];
     const long long off = a.req_off[r];
-    // F_{n+1} from the robot's frame n to its joint frame n': (R^T f, R^T (n - r x f))
-    BaseParams<T> bp = a.base;
+    // boundary terms in this robot's frames: V_0, dV_0 to D_{-1} (Ad_{G^-1}:
+    // (R^T (v + w x p), R^T w)); F_{n+1} from frame n to D_{n-1}:
+    // (R^T f, R^T (n - r x f))
+    BaseParams<T> bp;
     {
+        const T *g = a.robot_gb + (size_t)robot * 12;
+        const V3<T> p = mk3(g[9], g[10], g[11]);
+        const V3<T> v0 = mk3(a.base.V0[0], a.base.V0[1], a.base.V0[2]);
+        const V3<T> w0 = mk3(a.base.V0[3], a.base.V0[4], a.base.V0[5]);
+        const V3<T> a0 = mk3(a.base.dV0[0], a.base.dV0[1], a.base.dV0[2]);
+        const V3<T> al0 = mk3(a.base.dV0[3], a.base.dV0[4], a.base.dV0[5]);
+        const V3<T> vv = mulAT(g, cross_add(w0, p, v0)), ww = mulAT(g, w0);
+        const V3<T> aa = mulAT(g, cross_add(al0, p, a0)), al = mulAT(g, al0);
+        bp.V0[0] = vv.x; bp.V0[1] = vv.y; bp.V0[2] = vv.z;
+        bp.V0[3] = ww.x; bp.V0[4] = ww.y; bp.V0[5] = ww.z;
+        bp.dV0[0] = aa.x; bp.dV0[1] = aa.y; bp.dV0[2] = aa.z;
+        bp.dV0[3] = al.x; bp.dV0[4] = al.y; bp.dV0[5] = al.z;
         const T *tn = a.robot_tn + (size_t)robot * 12;
         const V3<T> f = mk3(a.base.Fn[0], a.base.Fn[1], a.base.Fn[2]);
         const V3<T> nn = mk3(a.base.Fn[3], a.base.Fn[4], a.base.Fn[5]);
@@ -113,17 +127,17 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int r)
         bp.Fn[0] = fp.x; bp.Fn[1] = fp.y; bp.Fn[2] = fp.z;
         bp.Fn[3] = np.x; bp.Fn[4] = np.y; bp.Fn[5] = np.z;
     }
-    const T *sc = a.consts + lo * kLinkConsts;
+    const T *sc = a.consts + lo * kDhConsts;
     if (a.req_kind[r] == 0) {
-        rnea_instance_recompute<T>(sc, n, a.q + off, a.qd + off, a.in2 + off, a.out + off, bp);
+        rnea_dh_instance<T, kTrigPoly>(sc, n, a.q + off, a.qd + off, a.in2 + off, a.out + off, bp);
     } else {
         unsigned char *w = a.ws + a.req_ws[r];
         T *wt = reinterpret_cast<T *>(w);
         double *wz = reinterpret_cast<double *>(
             w + (((size_t)n * kAbaStateScalars * sizeof(T) + 15) & ~(size_t)15));
-        const int bad = aba_instance<T, double, false>(sc, a.consts64 + lo * kLinkConsts, n,
-                                                       a.q + off, a.qd + off, a.in2 + off,
-                                                       a.out + off, wt, wz, 1, 0, bp);
+        const int bad = aba_dh_instance<T, double, kTrigPoly, false>(
+            sc, a.consts64 + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off, a.out + off,
+            wt, wz, 1, 0, bp);
         if (a.status) a.status[r] = bad ? 1 : 0;
     }
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <new>
 #include <numeric>
@@ -17,11 +18,12 @@ struct rd_fleet {
     int nrobots = 0;
     long long total_links = 0;
     std::vector<int> n;  // host copy
-    float *c32 = nullptr;
-    double *c64 = nullptr;
+    float *c32 = nullptr;     // [links][16] common-normal constants
+    double *c64 = nullptr;    // same in FP64
+    double *aba64 = nullptr;  // [links][32] FP64 forward-dynamics records
     int *robot_n = nullptr, *robot_link = nullptr;
-    float *tn32 = nullptr;
-    double *tn64 = nullptr;
+    float *gb32 = nullptr, *tn32 = nullptr;  // [robots][12] boundary frames
+    double *gb64 = nullptr, *tn64 = nullptr;
 };
 
 struct rd_plan {
@@ -59,8 +61,11 @@ extern "C" void rd_fleet_destroy(rd_fleet *f)
     if (!f) return;
     cudaFree(f->c32);
     cudaFree(f->c64);
+    cudaFree(f->aba64);
     cudaFree(f->robot_n);
     cudaFree(f->robot_link);
+    cudaFree(f->gb32);
+    cudaFree(f->gb64);
     cudaFree(f->tn32);
     cudaFree(f->tn64);
     delete f;
@@ -74,25 +79,37 @@ extern "C" int rd_fleet_create(int nrobots, const int *n, const double *M, const
     *out = nullptr;
     if (nrobots < 1) return rd_fail(RD_ERR_RANGE, "rd_fleet_create: nrobots = %d", nrobots);
     if (!n || !M || !S || !inertia) return rd_fail(RD_ERR_ARG, "rd_fleet_create: null array");
-    std::vector<double> all64;
+    std::vector<double> all64, allaba;
     std::vector<int> link(nrobots);
-    std::vector<double> tn((size_t)nrobots * 12);
+    std::vector<double> tn((size_t)nrobots * 12), gb((size_t)nrobots * 12);
     long long lo = 0;
     for (int r = 0; r < nrobots; ++r) {
         if (n[r] < 1 || n[r] > RD_MAX_LINKS)
             return rd_fail(RD_ERR_RANGE, "rd_fleet_create: robot %d has n = %d outside [1, %d]", r,
                            n[r], RD_MAX_LINKS);
-        std::vector<double> c;
-        double TnR[9], Tnp[3];
+        std::vector<double> c, dh, aba;
+        double TnR[9], Tnp[3], GBR[9], GBp[3], phi = 0.0;
         int rc = rd_build_chain(n[r], M + 12 * lo, S + 6 * lo, inertia + 10 * lo, c, TnR, Tnp);
+        if (rc == RD_OK) rc = rd_build_dh(n[r], c, dh, GBR, GBp, &phi);
         if (rc) {
             std::string msg = g_rd_error;
             return rd_fail(rc, "rd_fleet_create: robot %d: %s", r, msg.c_str());
         }
+        rd_build_aba64(n[r], dh, aba);
         link[r] = (int)lo;
-        all64.insert(all64.end(), c.begin(), c.end());
-        for (int k = 0; k < 9; ++k) tn[(size_t)r * 12 + k] = TnR[k];
+        all64.insert(all64.end(), dh.begin(), dh.end());
+        allaba.insert(allaba.end(), aba.begin(), aba.end());
+        // F_{n+1} goes from frame n to D_{n-1}: the joint frame of link n
+        // turned by phi about its z axis, R' = R Rz(phi), same origin
+        const double cp = std::cos(phi), sp = std::sin(phi);
+        for (int i = 0; i < 3; ++i) {
+            tn[(size_t)r * 12 + 3 * i + 0] = TnR[3 * i] * cp + TnR[3 * i + 1] * sp;
+            tn[(size_t)r * 12 + 3 * i + 1] = -TnR[3 * i] * sp + TnR[3 * i + 1] * cp;
+            tn[(size_t)r * 12 + 3 * i + 2] = TnR[3 * i + 2];
+        }
         for (int k = 0; k < 3; ++k) tn[(size_t)r * 12 + 9 + k] = Tnp[k];
+        for (int k = 0; k < 9; ++k) gb[(size_t)r * 12 + k] = GBR[k];
+        for (int k = 0; k < 3; ++k) gb[(size_t)r * 12 + 9 + k] = GBp[k];
         lo += n[r];
     }
     rd_fleet *f = new (std::nothrow) rd_fleet();
@@ -102,13 +119,16 @@ extern "C" int rd_fleet_create(int nrobots, const int *n, const double *M, const
     f->n.assign(n, n + nrobots);
     cudaError_t e = cudaGetDevice(&f->device);
     std::vector<float> all32(all64.begin(), all64.end());
-    std::vector<float> tn32(tn.begin(), tn.end());
+    std::vector<float> tn32(tn.begin(), tn.end()), gb32(gb.begin(), gb.end());
     if (e == cudaSuccess) e = upload(&f->c64, all64.data(), all64.size());
     if (e == cudaSuccess) e = upload(&f->c32, all32.data(), all32.size());
+    if (e == cudaSuccess) e = upload(&f->aba64, allaba.data(), allaba.size());
     if (e == cudaSuccess) e = upload(&f->robot_n, n, (size_t)nrobots);
     if (e == cudaSuccess) e = upload(&f->robot_link, link.data(), link.size());
     if (e == cudaSuccess) e = upload(&f->tn64, tn.data(), tn.size());
     if (e == cudaSuccess) e = upload(&f->tn32, tn32.data(), tn32.size());
+    if (e == cudaSuccess) e = upload(&f->gb64, gb.data(), gb.size());
+    if (e == cudaSuccess) e = upload(&f->gb32, gb32.data(), gb32.size());
     if (e != cudaSuccess) {
         rd_fleet_destroy(f);
         return rd_fail(RD_ERR_ALLOC, "rd_fleet_create: %s", cudaGetErrorString(e));
@@ -228,11 +248,13 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
     if constexpr (sizeof(T) == 4) {
         a.consts = f->c32;
         a.robot_tn = f->tn32;
+        a.robot_gb = f->gb32;
     } else {
         a.consts = f->c64;
         a.robot_tn = f->tn64;
+        a.robot_gb = f->gb64;
     }
-    a.consts64 = f->c64;
+    a.consts64 = f->aba64;
     a.robot_n = f->robot_n;
     a.robot_link = f->robot_link;
     a.order = p->order;

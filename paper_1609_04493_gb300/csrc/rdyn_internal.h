@@ -55,6 +55,7 @@ void rd_convert_base(const rd_model *m, const double *base, double out[18]);
 void rd_convert_base_dh(const rd_model *m, const double in18[18], double out[18]);
 int rd_build_dh(int n, const std::vector<double> &c64, std::vector<double> &dh64, double GBR[9],
                 double GBp[3], double *phi_last);
+void rd_build_aba64(int n, const std::vector<double> &dh64, std::vector<double> &out);
 int rd_rnea_dh_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
                    int kfull, int tmem, cudaStream_t s);

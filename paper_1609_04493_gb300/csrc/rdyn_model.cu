@@ -317,6 +317,35 @@ int rd_build_dh(int n, const std::vector<double> &c64, std::vector<double> &dh64
     return RD_OK;
 }
 
+// FP64 forward-dynamics records (aba_dh.cuh) from the common-normal constants:
+// the 16 constants, m c, C_o = I_c + m (|c|^2 - c c^T), cos^2 alpha, sin^2 alpha,
+// cos alpha sin alpha, cos 2 alpha, sin 2 alpha; 32 per link.
+void rd_build_aba64(int n, const std::vector<double> &dh64, std::vector<double> &out)
+{
+    out.assign((size_t)n * 32, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double *d = dh64.data() + (size_t)i * rdyn::kDhConsts;
+        double *r = out.data() + (size_t)i * 32;
+        for (int k = 0; k < rdyn::kDhConsts; ++k) r[k] = d[k];
+        const double m = d[6], cx = d[7], cy = d[8], cz = d[9];
+        r[16] = m * cx;
+        r[17] = m * cy;
+        r[18] = m * cz;
+        r[19] = d[10] + m * (cy * cy + cz * cz);
+        r[20] = d[11] + m * (cx * cx + cz * cz);
+        r[21] = d[12] + m * (cx * cx + cy * cy);
+        r[22] = d[13] - m * cx * cy;
+        r[23] = d[14] - m * cx * cz;
+        r[24] = d[15] - m * cy * cz;
+        const double ca = d[0], sa = d[1];
+        r[25] = ca * ca;
+        r[26] = sa * sa;
+        r[27] = ca * sa;
+        r[28] = ca * ca - sa * sa;
+        r[29] = 2.0 * ca * sa;
+    }
+}
+
 extern "C" int rd_model_create(int n, const double *M, const double *S, const double *inertia,
                                rd_model **out)
 {
@@ -350,30 +379,7 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
     }
     std::vector<float> dh32(dh64.begin(), dh64.end());
     mdl->host_dh64 = dh64;
-    // forward-dynamics records: the 16 constants, m c, C_o = I_c + m (|c|^2 - c c^T),
-    // cos^2 alpha, sin^2 alpha, cos alpha sin alpha, cos 2 alpha, sin 2 alpha
-    mdl->host_aba64.assign((size_t)n * 32, 0.0);
-    for (int i = 0; i < n; ++i) {
-        const double *d = dh64.data() + (size_t)i * rdyn::kDhConsts;
-        double *r = mdl->host_aba64.data() + (size_t)i * 32;
-        for (int k = 0; k < rdyn::kDhConsts; ++k) r[k] = d[k];
-        const double m = d[6], cx = d[7], cy = d[8], cz = d[9];
-        r[16] = m * cx;
-        r[17] = m * cy;
-        r[18] = m * cz;
-        r[19] = d[10] + m * (cy * cy + cz * cz);
-        r[20] = d[11] + m * (cx * cx + cz * cz);
-        r[21] = d[12] + m * (cx * cx + cy * cy);
-        r[22] = d[13] - m * cx * cy;
-        r[23] = d[14] - m * cx * cz;
-        r[24] = d[15] - m * cy * cz;
-        const double ca = d[0], sa = d[1];
-        r[25] = ca * ca;
-        r[26] = sa * sa;
-        r[27] = ca * sa;
-        r[28] = ca * ca - sa * sa;
-        r[29] = 2.0 * ca * sa;
-    }
+    rd_build_aba64(n, dh64, mdl->host_aba64);
 
     std::vector<float> c32(c64.size());
     for (size_t k = 0; k < c64.size(); ++k) c32[k] = (float)c64[k];
