@@ -2,9 +2,12 @@
 
 The paper names "an automatic scheduler for hardware-specific optimal
 performance" as future work (Sec. VI). Here the library exposes its choices as
-explicit variant codes (rnea_batch: per-thread serial recursion with one of
-four backward-state modes -- stored, stateless, cos/sin only, or stored for the
-first K links -- and a block size, or the lane-parallel scan with L lanes; fleet_batch: persistent CTA shape or one launch per group), and this
+explicit variant codes (rnea_batch: per-thread serial recursion in joint frames
+with one of four backward-state modes -- stored, stateless, cos/sin only, or
+stored for the first K links -- and a block size; the same in common-normal
+frames with the constants as a kernel parameter and K stored links, or with
+the state of the first links in tensor memory; or the lane-parallel scan with L
+lanes; fleet_batch: persistent CTA shape or one launch per group), and this
 module times the candidates on the caller's own data with CUDA events, keeps
 the fastest, and caches the answer in a JSON file keyed by GPU name, SM count
 and the workload's shape (RDYN_TUNE_CACHE, default ~/.cache/rdyn/tune.json).
@@ -69,7 +72,7 @@ def _time(torch, fn, reps=5):
 
 
 def rnea_candidates(n, B, dtype):
-    c = []
+    c = [b.RD_VARIANT_AUTO]
     for block in (32, 64, 128):
         for mode in (b.RD_VARIANT_SERIAL, b.RD_VARIANT_SERIAL_RECOMPUTE,
                      b.RD_VARIANT_SERIAL_RECOMPUTE_CS):
@@ -79,6 +82,17 @@ def rnea_candidates(n, B, dtype):
             if K < n:
                 c.append(b.RD_VARIANT_SERIAL_HYBRID | b.RD_TUNE_STORED_LINKS(K) |
                          b.RD_TUNE_BLOCK(block))
+    # common-normal frames: full state for the first K links (0 = library default)
+    for block in (32, 64):
+        c.append(b.RD_VARIANT_SERIAL_DH_RECOMPUTE | b.RD_TUNE_BLOCK(block))
+        for K in (0, 8, 12, 16, 20, 24, 32):
+            if K <= n:
+                c.append(b.RD_VARIANT_SERIAL_DH | b.RD_TUNE_STORED_LINKS(K) |
+                         b.RD_TUNE_BLOCK(block))
+    if n <= 32 and n % 4 == 0 and str(dtype) in ("torch.float32", "float32", "None"):
+        for K in (0, 16, 20, 24):  # state of the first links in tensor memory
+            if K <= n:
+                c.append(b.RD_VARIANT_SERIAL_DH_TMEM | b.RD_TUNE_STORED_LINKS(K))
     for lanes in (2, 4, 8, 16, 32):
         if n <= 8 * lanes:
             c.append(b.RD_VARIANT_SCAN(lanes))

@@ -35,3 +35,15 @@ def test_rnea_candidates_hybrid_store_fewer_links_than_the_chain():
             K = 4 * ((v >> 20) & 0xff)
             assert 0 < K < n
             assert ((v >> 16) & 0xf) in (5, 6)  # 32 or 64 threads
+
+
+def test_rnea_candidates_cover_the_common_normal_kernels():
+    """Stored-prefix lengths never exceed the chain; the tensor-memory variant is
+    offered only where it runs (FP32, n <= 32, n % 4 == 0)."""
+    for n, dt in ((8, "float32"), (32, "float32"), (32, "float64"), (36, "float32"), (100, None)):
+        cands = autotune.rnea_candidates(n, 65536, dt)
+        dh = [v for v in cands if (v & 0xfff) == b.RD_VARIANT_SERIAL_DH]
+        assert dh and all(4 * ((v >> 20) & 0xff) <= n for v in dh)
+        tm = [v for v in cands if (v & 0xfff) == b.RD_VARIANT_SERIAL_DH_TMEM]
+        assert bool(tm) == (n <= 32 and n % 4 == 0 and dt != "float64"), (n, dt)
+        assert b.RD_VARIANT_AUTO in cands
