@@ -75,16 +75,22 @@ VJP_ALGO_FLOP_PER_LINK = 1400
 # forward dynamics per link (articulated-body algorithm), FMA = 2: ~720 FP32
 # flop (bias motion and wrenches, backward wrench carry, z_hat / lambda
 # transforms) and ~800 FP64 flop (articulated-inertia congruence, the rank-one
-# update and the Omega solves), the split of the design's precision plan
+# update and the Omega solves), the split of the design's precision plan (the
+# latter in FP64 or double-float arithmetic)
 FD_FLOP32_PER_LINK = 720
 FD_FLOP64_PER_LINK = 800
-# executed arithmetic of the common-normal forward-dynamics kernel per link:
-# FP32 257 (sin/cos 26, products 4, bias motion 86, bias wrench 93, wrench carry
-# 44, products 4); FP64 400 (projected inertia 35, two plane rotations and the
-# shift of the articulated-inertia update 235, z_hat carry 60, Omega solve 12,
-# lambda step 56)
+# executed arithmetic of the common-normal forward-dynamics kernel per link with
+# the FP64 update: FP32 257 (sin/cos 26, products 4, bias motion 86, bias wrench
+# 93, wrench carry 44, products 4); FP64 400 (projected inertia 35, two plane
+# rotations and the shift of the articulated-inertia update 235, z_hat carry
+# 60, Omega solve 12, lambda step 56)
 FD_EXEC_FLOP32_PER_LINK = 257
 FD_EXEC_FLOP64_PER_LINK = 400
+# the default for FP32 data carries those FP64 operations in double-float
+# arithmetic on the FP32 pipe: FP32-pipe instructions executed per link, from
+# the FMA-pipe count of an ncu capture at n = 64, B = 16384 (105.4 M warp
+# instructions, 94% of all)
+FD_DF_EXEC_FP32_INST_PER_LINK = 3217
 # bytes an inverse-dynamics link of the uneven workload moves: q, qd, qdd, tau
 # (16) plus its robot's constants streamed per request (112)
 UNEVEN_ID_BYTES_PER_LINK = 128
@@ -234,11 +240,6 @@ def fp32_peak_tflops():
     return SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
 
 
-def fd_algorithmic_seconds_per_link():
-    return (FD_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
-            + FD_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
-
-
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -349,26 +350,40 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
         ws = torch.empty(rd.aba_workspace_bytes(model, B, 0), dtype=torch.uint8, device=dev)
         o = torch.empty_like(sets[0][0])
         steps = max(3, min(K, 50))
+        inst_rate = SM_COUNT * FP32_LANES_PER_SM * 2.070e9  # FP32-pipe thread instructions/s
 
-        def call(k):
-            x = sets[k % len(sets)]
-            rd.aba(model, *x, workspace=ws, out=o)
+        def timed(flags):
+            def call(k):
+                x = sets[k % len(sets)]
+                rd.aba(model, *x, workspace=ws, out=o, flags=flags)
+            return time_calls(torch, call, steps, 3, dist, sampler)
 
-        t = time_calls(torch, call, steps, 3, dist, sampler)
-        t_alg = B * n * fd_algorithmic_seconds_per_link()
-        t_exec = B * n * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
-                          + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
+        t = timed(0)
+        t64 = timed(rd.RD_ABA_FP64_UPDATE)
+        t_exec = B * n * FD_DF_EXEC_FP32_INST_PER_LINK / inst_rate
+        t_floor = B * n * FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12)
+        t_exec64 = B * n * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
+                            + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
         out[f"n{n}_B{B}"] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
                              "steps": steps, "roofline_ms": t_exec * 1e3,
                              "roofline_frac": t_exec / (t / steps),
-                             "algorithmic_roofline_ms": t_alg * 1e3,
-                             "algorithmic_roofline_frac": t_alg / (t / steps)}
-    out["metric"] = ("forward dynamics (articulated-body, FP32 data, FP64 inertia updates and "
-                     "solves) evals/s")
-    out["roofline"] = (f"combined FP32 + FP64 time of the kernel's {FD_EXEC_FLOP32_PER_LINK} FP32 "
-                       f"and {FD_EXEC_FLOP64_PER_LINK} FP64 flop per link at the derived FP32 and "
-                       f"nominal FP64 peaks, divided by the measured time; algorithmic: the same "
-                       f"with {FD_FLOP32_PER_LINK} and {FD_FLOP64_PER_LINK} flop per link")
+                             "fp64_pipe_floor_ms": t_floor * 1e3,
+                             "fp64_update": {"value": B * steps / t64,
+                                             "ms_per_step": t64 / steps * 1e3,
+                                             "roofline_ms": t_exec64 * 1e3,
+                                             "roofline_frac": t_exec64 / (t64 / steps)}}
+    out["algorithmic_flop_per_link"] = {"fp32": FD_FLOP32_PER_LINK,
+                                         "extended_precision": FD_FLOP64_PER_LINK}
+    out["metric"] = ("forward dynamics (articulated-body, FP32 data; inertia updates and solves "
+                     "in double-float arithmetic, and beside it in FP64) evals/s")
+    out["roofline"] = (f"double-float default: FP32-pipe issue time of the kernel's "
+                       f"{FD_DF_EXEC_FP32_INST_PER_LINK} FP32 instructions per link at "
+                       f"{SM_COUNT} x {FP32_LANES_PER_SM} lanes x 2.07 GHz, divided by the "
+                       f"measured time; fp64_pipe_floor_ms: the time the FP64 pipe needs for the "
+                       f"update's {FD_EXEC_FLOP64_PER_LINK} FP64 flop per link at the nominal "
+                       f"FP64 peak, which the FP64 kernel cannot beat; fp64_update: combined FP32 "
+                       f"+ FP64 time of its {FD_EXEC_FLOP32_PER_LINK} FP32 and "
+                       f"{FD_EXEC_FLOP64_PER_LINK} FP64 flop per link")
     return out
 
 
@@ -400,17 +415,19 @@ def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
     n_id = J - n_fd
     t_alg = (n_id * max(ALGO_FLOP_PER_LINK / (fp32_peak_tflops() * 1e12),
                         UNEVEN_ID_BYTES_PER_LINK / (measured_peaks().get("hbm_gbs", 6800.0) * 1e9))
-             + n_fd * fd_algorithmic_seconds_per_link())
+             + n_fd * FD_DF_EXEC_FP32_INST_PER_LINK / (SM_COUNT * FP32_LANES_PER_SM * 2.070e9))
     for name in ("persistent_tuned", "per_group_launches"):
         res[name]["roofline_frac"] = t_alg / (res[name]["ms_per_step"] * 1e-3)
     res["roofline_ms"] = t_alg * 1e3
     res["roofline"] = (f"inverse dynamics links at the larger of {ALGO_FLOP_PER_LINK} flop / FP32 "
                        f"peak and {UNEVEN_ID_BYTES_PER_LINK} B (joint values, torque, streamed "
                        f"constants) / measured HBM bandwidth, plus forward dynamics links at the "
-                       f"combined FP32 + FP64 time; divided by the measured time")
+                       f"FP32-pipe issue time of the double-float kernel's "
+                       f"{FD_DF_EXEC_FP32_INST_PER_LINK} instructions per link; divided by the "
+                       f"measured time")
     res["workload"] = (f"{count} requests, own robot each, n uniform in 6..100 "
                        f"({J} joints), {int(kinds.sum())} forward / {count - int(kinds.sum())} "
-                       f"inverse dynamics, FP32 (FP64 inertia updates and solves)")
+                       f"inverse dynamics, FP32 (double-float inertia updates and solves)")
     res["launches_per_group_schedule"] = plan.groups
     return res
 

@@ -378,6 +378,7 @@ def rnea_autograd(model, q, qd, qdd, base=None, vjp_mode=RD_VJP_RECOMPUTE):
 
 RD_ABA_SCANS_IN_DTYPE = 0x1
 RD_ABA_JOINT_FRAMES = 0x2
+RD_ABA_FP64_UPDATE = 0x4
 
 
 def aba_workspace_bytes(model, B, dtype_code, flags=0):
@@ -550,13 +551,13 @@ def forward_dynamics(model, q, qd, tau, method="auto", base=None, status=None, w
     """qdd = FD(q, qd, tau) by the articulated-body algorithm (aba_batch) or the
     joint-space-inertia solve (jsiia_batch). ``auto`` follows the crossover
     measured on GB300: JSIIA for FP32 chains of at most 32 links in batches of
-    at most 1536 (each instance spread over a warp; e.g. n = 32, B = 1024:
-    165 us vs 286 us), the articulated-body algorithm otherwise (e.g. n = 32,
-    B = 2048: 286 us vs 311 us; B = 8192: 286 us vs 1034 us; FP64: always)."""
+    at most 512 (each instance spread over a warp; e.g. n = 32, B = 256: 111 us
+    vs 142 us), the articulated-body algorithm otherwise (e.g. n = 32,
+    B = 1024: 140 us vs 165 us; B = 8192: 159 us vs 1034 us; FP64: always)."""
     import torch
 
     if method == "auto":
-        small = q.shape[0] <= 1536 and model.n <= 32 and q.dtype == torch.float32
+        small = q.shape[0] <= 512 and model.n <= 32 and q.dtype == torch.float32
         method = "jsiia" if small else "aba"
     if method == "jsiia":
         return jsiia(model, q, qd, tau, base=base, status=status, out=out, stream=stream)

@@ -31,18 +31,24 @@ namespace rdyn {
 
 constexpr int kAbaStateScalars = 10;
 
-struct Sym3d {
-    double xx, yy, zz, xy, xz, yz;
+// symmetric 3x3 in the scalar D (double, or the double-float pair of df.cuh)
+template <typename D>
+struct Sym3 {
+    D xx, yy, zz, xy, xz, yz;
 };
+using Sym3d = Sym3<double>;
 
 // 6x6 symmetric [[A, Bm], [Bm^T, C]] in twist order (v, w)
-struct Abi {
-    Sym3d A;
-    double Bm[9];  // row-major
-    Sym3d C;
+template <typename D>
+struct AbiT {
+    Sym3<D> A;
+    D Bm[9];  // row-major
+    Sym3<D> C;
 };
+using Abi = AbiT<double>;
 
-__device__ __forceinline__ void sym_to_full(const Sym3d &s, double m[9])
+template <typename D>
+__device__ __forceinline__ void sym_to_full(const Sym3<D> &s, D m[9])
 {
     m[0] = s.xx; m[1] = s.xy; m[2] = s.xz;
     m[3] = s.xy; m[4] = s.yy; m[5] = s.yz;
@@ -81,11 +87,12 @@ __device__ __forceinline__ Sym3d rot_congr_sym(const double R[9], const Sym3d &s
 }
 
 // [b] X (each column crossed with b)
-__device__ __forceinline__ void hat_mul(const double b[3], const double X[9], double out[9])
+template <typename D>
+__device__ __forceinline__ void hat_mul(const D b[3], const D X[9], D out[9])
 {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const double x0 = X[j], x1 = X[3 + j], x2 = X[6 + j];
+        const D x0 = X[j], x1 = X[3 + j], x2 = X[6 + j];
         out[j] = fma(b[1], x2, -b[2] * x1);
         out[3 + j] = fma(b[2], x0, -b[0] * x2);
         out[6 + j] = fma(b[0], x1, -b[1] * x0);

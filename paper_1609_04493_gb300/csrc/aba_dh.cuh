@@ -19,8 +19,16 @@
 // * Then the shift by b, as in aba.cuh.
 // J_i about the frame origin is precomputed on the host (FP64 record below).
 // For n % 4 == 0, n <= NMAX and 16-byte aligned rows.
+//
+// The scalar D of the inertia update and the solves is double, or for FP32
+// data optionally the double-float pair of df.cuh (about 48 bits, computed on
+// the FP32 pipe): the records then hold each FP64 constant split into a pair
+// on the host, and the z_hat / lambda recursions run in D too.
 #pragma once
+#include <type_traits>
+
 #include "aba.cuh"
+#include "df.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
@@ -31,81 +39,85 @@ namespace rdyn {
 // alpha, cos 2 alpha, sin 2 alpha; 2 pad.
 constexpr int kAbaDh64 = 32;
 
-template <typename T, int NMAX>
+// D: double, or DF (df.cuh) for the double-float variant
+template <typename T, typename D, int NMAX>
 struct AbaDhConsts {
     T c[NMAX * kDhConsts];    // in the data precision, for the FP32 (or FP64) sweeps
-    double d[NMAX * kAbaDh64];
+    D d[NMAX * kAbaDh64];
 };
 
 // S' = Rz S Rz^T for symmetric S (double angle c2 = cos 2t, s2 = sin 2t)
-__device__ __forceinline__ Sym3d rotz_sym(const Sym3d &S, double c, double s, double c2, double s2)
+template <typename D>
+__device__ __forceinline__ Sym3<D> rotz_sym(const Sym3<D> &S, D c, D s, D c2, D s2)
 {
-    const double h = 0.5 * (S.xx + S.yy), d = 0.5 * (S.xx - S.yy);
-    const double t = fma(d, c2, -S.xy * s2);
-    return Sym3d{h + t, h - t, S.zz, fma(d, s2, S.xy * c2), fma(c, S.xz, -s * S.yz),
-                 fma(s, S.xz, c * S.yz)};
+    const D h = dhalf(S.xx + S.yy), d = dhalf(S.xx - S.yy);
+    const D t = fma(d, c2, -S.xy * s2);
+    return Sym3<D>{h + t, h - t, S.zz, fma(d, s2, S.xy * c2), fma(c, S.xz, -s * S.yz),
+                   fma(s, S.xz, c * S.yz)};
 }
 
 // S' = Rx S Rx^T for symmetric S: the (y, z) plane
-__device__ __forceinline__ Sym3d rotx_sym(const Sym3d &S, double ca, double sa, double c2, double s2)
+template <typename D>
+__device__ __forceinline__ Sym3<D> rotx_sym(const Sym3<D> &S, D ca, D sa, D c2, D s2)
 {
-    const double h = 0.5 * (S.yy + S.zz), d = 0.5 * (S.yy - S.zz);
-    const double t = fma(d, c2, -S.yz * s2);
-    return Sym3d{S.xx, h + t, h - t, fma(ca, S.xy, -sa * S.xz), fma(sa, S.xy, ca * S.xz),
-                 fma(d, s2, S.yz * c2)};
+    const D h = dhalf(S.yy + S.zz), d = dhalf(S.yy - S.zz);
+    const D t = fma(d, c2, -S.yz * s2);
+    return Sym3<D>{S.xx, h + t, h - t, fma(ca, S.xy, -sa * S.xz), fma(sa, S.xy, ca * S.xz),
+                   fma(d, s2, S.yz * c2)};
 }
 
 // X^T P X + J_i for the projected articulated inertia P of link i+1 (zero w_z
 // row and column) and the transform of link i+1 (cos/sin of theta, record r).
-__device__ __forceinline__ Abi aba_dh_update(const Abi &P, double c, double s, const double *r,
-                                             const double *ri)
+template <typename D>
+__device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, const D *r,
+                                                 const D *ri)
 {
-    const double ca = r[0], sa = r[1];
-    const double ca2 = r[25], sa2 = r[26], casa = r[27], c2a = r[28], s2a = r[29];
-    const double c2 = fma(c, c, -s * s), s2 = 2.0 * c * s;
+    const D ca = r[0], sa = r[1];
+    const D ca2 = r[25], sa2 = r[26], casa = r[27], c2a = r[28], s2a = r[29];
+    const D c2 = fma(c, c, -s * s), s2 = dtwice(c * s);
     // rotation about z: A full, Bm with a zero last column, C with its xy part only
-    Abi M;
+    AbiT<D> M;
     M.A = rotz_sym(P.A, c, s, c2, s2);
-    double B1[6];  // rows 0..2, columns 0..1 of Rz Bm (rows mixed)
+    D B1[6];  // rows 0..2, columns 0..1 of Rz Bm (rows mixed)
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         B1[k] = fma(c, P.Bm[k], -s * P.Bm[3 + k]);
         B1[2 + k] = fma(s, P.Bm[k], c * P.Bm[3 + k]);
         B1[4 + k] = P.Bm[6 + k];
     }
-    double B2[6];  // then columns mixed (Bm Rz^T)
+    D B2[6];  // then columns mixed (Bm Rz^T)
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr) {
         B2[2 * rr] = fma(c, B1[2 * rr], -s * B1[2 * rr + 1]);
         B2[2 * rr + 1] = fma(s, B1[2 * rr], c * B1[2 * rr + 1]);
     }
-    const double hc = 0.5 * (P.C.xx + P.C.yy), dc = 0.5 * (P.C.xx - P.C.yy);
-    const double tc = fma(dc, c2, -P.C.xy * s2);
-    const double Cxx = hc + tc, Cyy = hc - tc, Cxy = fma(dc, s2, P.C.xy * c2);
+    const D hc = dhalf(P.C.xx + P.C.yy), dc = dhalf(P.C.xx - P.C.yy);
+    const D tc = fma(dc, c2, -P.C.xy * s2);
+    const D Cxx = hc + tc, Cyy = hc - tc, Cxy = fma(dc, s2, P.C.xy * c2);
     // rotation about x
     M.A = rotx_sym(M.A, ca, sa, c2a, s2a);
     // Bm: rows 1, 2 mixed (columns 0, 1), then columns: col1 -> ca col1, col2 = sa col1
-    double Br[9];
+    D Br[9];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const double y = B2[2 + k], z = B2[4 + k];
+        const D y = B2[2 + k], z = B2[4 + k];
         Br[k] = B2[k];
         Br[3 + k] = fma(ca, y, -sa * z);
         Br[6 + k] = fma(sa, y, ca * z);
     }
 #pragma unroll
     for (int rr = 0; rr < 3; ++rr) {
-        const double col1 = Br[3 * rr + 1];
+        const D col1 = Br[3 * rr + 1];
         Br[3 * rr + 1] = ca * col1;
         Br[3 * rr + 2] = sa * col1;
     }
-    M.C = Sym3d{Cxx, ca2 * Cyy, sa2 * Cyy, ca * Cxy, sa * Cxy, casa * Cyy};
+    M.C = Sym3<D>{Cxx, ca2 * Cyy, sa2 * Cyy, ca * Cxy, sa * Cxy, casa * Cyy};
 #pragma unroll
     for (int k = 0; k < 9; ++k) M.Bm[k] = Br[k];
     // shift by b (aba.cuh): A' = A_r, B' = B_r - A_r [b],
     // C' = C_r + [b]B_r - B_r^T[b] - [b]A_r[b]; then + J_i (A = m I, Bm = -[m c], C = C_o)
-    const double b[3] = {r[2], r[3], r[4]};
-    double Ar[9], Pm[9], PT[9], Nr[9], Q2[9];
+    const D b[3] = {r[2], r[3], r[4]};
+    D Ar[9], Pm[9], PT[9], Nr[9], Q2[9];
     sym_to_full(M.A, Ar);
     hat_mul(b, Ar, Pm);  // [b] A_r; its transpose is -A_r [b]
 #pragma unroll
@@ -114,9 +126,9 @@ __device__ __forceinline__ Abi aba_dh_update(const Abi &P, double c, double s, c
         for (int j = 0; j < 3; ++j) PT[3 * i + j] = Pm[3 * j + i];
     hat_mul(b, M.Bm, Nr);  // [b] B_r
     hat_mul(b, PT, Q2);    // -[b] A_r [b]
-    const double m = ri[6], mcx = ri[16], mcy = ri[17], mcz = ri[18];
-    Abi o;
-    o.A = Sym3d{M.A.xx + m, M.A.yy + m, M.A.zz + m, M.A.xy, M.A.xz, M.A.yz};
+    const D m = ri[6], mcx = ri[16], mcy = ri[17], mcz = ri[18];
+    AbiT<D> o;
+    o.A = Sym3<D>{M.A.xx + m, M.A.yy + m, M.A.zz + m, M.A.xy, M.A.xz, M.A.yz};
     o.Bm[0] = M.Bm[0] + PT[0];
     o.Bm[1] = M.Bm[1] + PT[1] + mcz;
     o.Bm[2] = M.Bm[2] + PT[2] - mcy;
@@ -126,22 +138,24 @@ __device__ __forceinline__ Abi aba_dh_update(const Abi &P, double c, double s, c
     o.Bm[6] = M.Bm[6] + PT[6] + mcy;
     o.Bm[7] = M.Bm[7] + PT[7] - mcx;
     o.Bm[8] = M.Bm[8] + PT[8];
-    o.C.xx = M.C.xx + 2.0 * Nr[0] + Q2[0] + ri[19];
-    o.C.yy = M.C.yy + 2.0 * Nr[4] + Q2[4] + ri[20];
-    o.C.zz = M.C.zz + 2.0 * Nr[8] + Q2[8] + ri[21];
-    o.C.xy = M.C.xy + Nr[1] + Nr[3] + 0.5 * (Q2[1] + Q2[3]) + ri[22];
-    o.C.xz = M.C.xz + Nr[2] + Nr[6] + 0.5 * (Q2[2] + Q2[6]) + ri[23];
-    o.C.yz = M.C.yz + Nr[5] + Nr[7] + 0.5 * (Q2[5] + Q2[7]) + ri[24];
+    o.C.xx = M.C.xx + dtwice(Nr[0]) + Q2[0] + ri[19];
+    o.C.yy = M.C.yy + dtwice(Nr[4]) + Q2[4] + ri[20];
+    o.C.zz = M.C.zz + dtwice(Nr[8]) + Q2[8] + ri[21];
+    o.C.xy = M.C.xy + Nr[1] + Nr[3] + dhalf(Q2[1] + Q2[3]) + ri[22];
+    o.C.xz = M.C.xz + Nr[2] + Nr[6] + dhalf(Q2[2] + Q2[6]) + ri[23];
+    o.C.yz = M.C.yz + Nr[5] + Nr[7] + dhalf(Q2[5] + Q2[7]) + ri[24];
     return o;
 }
 
 // One forward-dynamics instance in common-normal frames. sc: the chain's 16
-// constants per link in T; sd: its FP64 records; qr, qdr, taur, qddr: its joint
-// rows (VEC: n % 4 == 0 and 16-byte aligned, else element loads); ws / wsz and
-// (B, b): its workspace (aba_put). Returns 1 when an Omega_i <= 0 or a
-// non-finite qdd appeared.
-template <typename T, typename Z, int TRIG, bool VEC>
-__device__ __forceinline__ int aba_dh_instance(const T *sc, const double *sd, int n,
+// constants per link in T; sd: its records in D (FP64, or split into
+// double-float pairs); qr, qdr, taur, qddr: its joint rows (VEC: n % 4 == 0 and
+// 16-byte aligned, else element loads); ws / wsz and (B, b): its workspace
+// (aba_put; Z is the type of the solve state and of the z_hat / lambda
+// recursions: D, or T). Returns 1 when an Omega_i <= 0 or a non-finite qdd
+// appeared.
+template <typename T, typename D, typename Z, int TRIG, bool VEC>
+__device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
                                                const T *__restrict__ qr, const T *__restrict__ qdr,
                                                const T *__restrict__ taur, T *__restrict__ qddr,
                                                T *__restrict__ ws, Z *__restrict__ wsz, int B, int b,
@@ -178,137 +192,159 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const double *sd, in
         }
     }
 
-    // ---- sweep 2: tau_hat, articulated inertias (FP64), z_hat, c_hat
+    // ---- sweep 2: tau_hat, articulated inertias (D), z_hat, c_hat
+    // (Z = D: the transform of the z_hat step comes from the D records)
+    constexpr bool kZrec = std::is_same<Z, D>::value;
+    // The double-float body is about ten times the FP64 one in instructions:
+    // unrolled four links deep it no longer fits the instruction cache, and
+    // at one warp per scheduler every miss stalls issue. Its sweeps run one
+    // link per iteration.
+    constexpr bool kRolled = std::is_same<D, DF>::value;
     Wrench<T> F;
     F.f = mk3(base.Fn[0], base.Fn[1], base.Fn[2]);
     F.n = mk3(base.Fn[3], base.Fn[4], base.Fn[5]);
     Wrench<Z> z;
     z.f = z.n = mk3(Z(0), Z(0), Z(0));
-    Abi Jh;
-    double Uv[3] = {0, 0, 0}, Uw[3] = {0, 0, 0}, invOm = 0.0, chat = 0.0;
+    AbiT<D> Jh;
+    D Uv[3] = {D(0), D(0), D(0)}, Uw[3] = {D(0), D(0), D(0)}, invOm = D(0), chat = D(0);
     DhRot<T> Rn = dh_rot(T(1), T(0), T(1), T(0));
     V3<T> bn = mk3(T(0), T(0), T(0));
     DhRot<Z> RnZ = dh_rot(Z(1), Z(0), Z(1), Z(0));
     V3<Z> bnZ = mk3(Z(0), Z(0), Z(0));
-    double cn = 1.0, sn = 0.0;  // cos, sin of link i+1 in FP64
-    for (int i0 = ((n - 1) / 4) * 4; i0 >= 0; i0 -= 4) {
-        const Chunk<T> ct = ld_chunk<T, VEC>(taur, i0, n);
+    D cn = D(1), sn = D(0);  // cos, sin of link i+1 in D
+    // one link of the sweep, given tau_i
+    auto step2 = [&](int i, T tau_i) {
+        Wrench<T> Fh;
+        Fh.f = mk3(aba_get(ws, B, b, i, 0), aba_get(ws, B, b, i, 1), aba_get(ws, B, b, i, 2));
+        Fh.n = mk3(aba_get(ws, B, b, i, 3), aba_get(ws, B, b, i, 4), aba_get(ws, B, b, i, 5));
+        const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
+        const D *ri = sd + i * kAbaDh64;
+        if (i == n - 1) {
+            F.f = add3(F.f, Fh.f);
+            F.n = add3(F.n, Fh.n);
+            const D m = ri[6], zero = D(0);
+            Jh.A = Sym3<D>{m, m, m, zero, zero, zero};
+            Jh.Bm[0] = zero;    Jh.Bm[1] = ri[18];  Jh.Bm[2] = -ri[17];
+            Jh.Bm[3] = -ri[18]; Jh.Bm[4] = zero;    Jh.Bm[5] = ri[16];
+            Jh.Bm[6] = ri[17];  Jh.Bm[7] = -ri[16]; Jh.Bm[8] = zero;
+            Jh.C = Sym3<D>{ri[19], ri[20], ri[21], ri[22], ri[23], ri[24]};
+        } else {
+            F = dh_carry(Rn, bn, F, Fh);
+            // P = J_hat_{i+1} - U U^T / Omega: its w_z row and column vanish
+            AbiT<D> P;
+            const D ux = Uv[0] * invOm, uy = Uv[1] * invOm, uz = Uv[2] * invOm;
+            const D wx = Uw[0] * invOm, wy = Uw[1] * invOm;
+            P.A = Sym3<D>{fma(-ux, Uv[0], Jh.A.xx), fma(-uy, Uv[1], Jh.A.yy),
+                          fma(-uz, Uv[2], Jh.A.zz), fma(-ux, Uv[1], Jh.A.xy),
+                          fma(-ux, Uv[2], Jh.A.xz), fma(-uy, Uv[2], Jh.A.yz)};
 #pragma unroll
-        for (int j = 3; j >= 0; --j) {
-            const int i = i0 + j;
-            if (!(VEC || i < n)) continue;
-            Wrench<T> Fh;
-            Fh.f = mk3(aba_get(ws, B, b, i, 0), aba_get(ws, B, b, i, 1), aba_get(ws, B, b, i, 2));
-            Fh.n = mk3(aba_get(ws, B, b, i, 3), aba_get(ws, B, b, i, 4), aba_get(ws, B, b, i, 5));
-            const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
-            const double *ri = sd + i * kAbaDh64;
-            if (i == n - 1) {
-                F.f = add3(F.f, Fh.f);
-                F.n = add3(F.n, Fh.n);
-                const double m = ri[6];
-                Jh.A = Sym3d{m, m, m, 0.0, 0.0, 0.0};
-                Jh.Bm[0] = 0.0;     Jh.Bm[1] = ri[18];  Jh.Bm[2] = -ri[17];
-                Jh.Bm[3] = -ri[18]; Jh.Bm[4] = 0.0;     Jh.Bm[5] = ri[16];
-                Jh.Bm[6] = ri[17];  Jh.Bm[7] = -ri[16]; Jh.Bm[8] = 0.0;
-                Jh.C = Sym3d{ri[19], ri[20], ri[21], ri[22], ri[23], ri[24]};
-            } else {
-                F = dh_carry(Rn, bn, F, Fh);
-                // P = J_hat_{i+1} - U U^T / Omega: its w_z row and column vanish
-                Abi P;
-                const double ux = Uv[0] * invOm, uy = Uv[1] * invOm, uz = Uv[2] * invOm;
-                const double wx = Uw[0] * invOm, wy = Uw[1] * invOm;
-                P.A = Sym3d{fma(-ux, Uv[0], Jh.A.xx), fma(-uy, Uv[1], Jh.A.yy),
-                            fma(-uz, Uv[2], Jh.A.zz), fma(-ux, Uv[1], Jh.A.xy),
-                            fma(-ux, Uv[2], Jh.A.xz), fma(-uy, Uv[2], Jh.A.yz)};
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    P.Bm[3 * r] = fma(-Uv[r], wx, Jh.Bm[3 * r]);
-                    P.Bm[3 * r + 1] = fma(-Uv[r], wy, Jh.Bm[3 * r + 1]);
-                    P.Bm[3 * r + 2] = 0.0;
-                }
-                P.C = Sym3d{fma(-wx, Uw[0], Jh.C.xx), fma(-wy, Uw[1], Jh.C.yy), 0.0,
-                            fma(-wx, Uw[1], Jh.C.xy), 0.0, 0.0};
-                Jh = aba_dh_update(P, cn, sn, sd + (i + 1) * kAbaDh64, ri);
-                // z_hat_i = X^T (z_hat_{i+1} + U_{i+1} c_hat_{i+1})
-                Wrench<Z> zz;
-                zz.f = mk3(z.f.x + (Z)(Uv[0] * chat), z.f.y + (Z)(Uv[1] * chat), z.f.z + (Z)(Uv[2] * chat));
-                zz.n = mk3(z.n.x + (Z)(Uw[0] * chat), z.n.y + (Z)(Uw[1] * chat), z.n.z + (Z)(Uw[2] * chat));
-                Wrench<Z> zero;
-                zero.f = zero.n = mk3(Z(0), Z(0), Z(0));
-                z = dh_carry(RnZ, bnZ, zz, zero);
+            for (int r = 0; r < 3; ++r) {
+                P.Bm[3 * r] = fma(-Uv[r], wx, Jh.Bm[3 * r]);
+                P.Bm[3 * r + 1] = fma(-Uv[r], wy, Jh.Bm[3 * r + 1]);
+                P.Bm[3 * r + 2] = D(0);
             }
-            const double tau_hat = (double)ct.v[j] - (double)F.n.z;
-            Uv[0] = Jh.Bm[2]; Uv[1] = Jh.Bm[5]; Uv[2] = Jh.Bm[8];
-            Uw[0] = Jh.C.xz; Uw[1] = Jh.C.yz; Uw[2] = Jh.C.zz;
-            const double Om = Jh.C.zz;
-            if (!(Om > 0.0)) bad = 1;
-            invOm = 1.0 / Om;
-            chat = (tau_hat - (double)z.n.z) * invOm;
-            const Z vals[8] = {(Z)Uv[0], (Z)Uv[1], (Z)Uv[2], (Z)Uw[0], (Z)Uw[1], (Z)Uw[2],
-                               (Z)chat, (Z)invOm};
+            P.C = Sym3<D>{fma(-wx, Uw[0], Jh.C.xx), fma(-wy, Uw[1], Jh.C.yy), D(0),
+                          fma(-wx, Uw[1], Jh.C.xy), D(0), D(0)};
+            Jh = aba_dh_update(P, cn, sn, sd + (i + 1) * kAbaDh64, ri);
+            // z_hat_i = X^T (z_hat_{i+1} + U_{i+1} c_hat_{i+1})
+            Wrench<Z> zz;
+            zz.f = mk3(z.f.x + dcvt<Z>(Uv[0] * chat), z.f.y + dcvt<Z>(Uv[1] * chat),
+                       z.f.z + dcvt<Z>(Uv[2] * chat));
+            zz.n = mk3(z.n.x + dcvt<Z>(Uw[0] * chat), z.n.y + dcvt<Z>(Uw[1] * chat),
+                       z.n.z + dcvt<Z>(Uw[2] * chat));
+            Wrench<Z> zero;
+            zero.f = zero.n = mk3(Z(0), Z(0), Z(0));
+            z = dh_carry(RnZ, bnZ, zz, zero);
+        }
+        const D tau_hat = dsub_exact<D>(tau_i, F.n.z);
+        Uv[0] = Jh.Bm[2]; Uv[1] = Jh.Bm[5]; Uv[2] = Jh.Bm[8];
+        Uw[0] = Jh.C.xz; Uw[1] = Jh.C.yz; Uw[2] = Jh.C.zz;
+        const D Om = Jh.C.zz;
+        if (!dpositive(Om)) bad = 1;
+        invOm = drecip(Om);
+        chat = (tau_hat - dcvt<D>(z.n.z)) * invOm;
+        const Z vals[8] = {dcvt<Z>(Uv[0]), dcvt<Z>(Uv[1]), dcvt<Z>(Uv[2]), dcvt<Z>(Uw[0]),
+                           dcvt<Z>(Uw[1]), dcvt<Z>(Uw[2]), dcvt<Z>(chat), dcvt<Z>(invOm)};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) aba_zput(wsz, B, b, i, k, vals[k]);
-            // transform of link i, for the step to link i-1
-            const T *Lt = sc + i * kDhConsts;
-            Rn = dh_rot(Lt[0], Lt[1], c, s);
-            bn = mk3(Lt[2], Lt[3], Lt[4]);
-            cn = (double)c;
-            sn = (double)s;
-            if constexpr (sizeof(Z) == 8) {
-                RnZ = dh_rot(ri[0], ri[1], cn, sn);
-                bnZ = mk3(ri[2], ri[3], ri[4]);
-            } else {
-                RnZ = dh_rot((Z)Lt[0], (Z)Lt[1], (Z)c, (Z)s);
-                bnZ = mk3((Z)Lt[2], (Z)Lt[3], (Z)Lt[4]);
-            }
+        for (int k = 0; k < 8; ++k) aba_zput(wsz, B, b, i, k, vals[k]);
+        // transform of link i, for the step to link i-1
+        const T *Lt = sc + i * kDhConsts;
+        Rn = dh_rot(Lt[0], Lt[1], c, s);
+        bn = mk3(Lt[2], Lt[3], Lt[4]);
+        cn = dcvt<D>(c);
+        sn = dcvt<D>(s);
+        if constexpr (kZrec) {
+            RnZ = dh_rot(ri[0], ri[1], cn, sn);
+            bnZ = mk3(ri[2], ri[3], ri[4]);
+        } else {
+            RnZ = dh_rot(dcvt<Z>(Lt[0]), dcvt<Z>(Lt[1]), dcvt<Z>(c), dcvt<Z>(s));
+            bnZ = mk3(dcvt<Z>(Lt[2]), dcvt<Z>(Lt[3]), dcvt<Z>(Lt[4]));
+        }
+    };
+    if constexpr (kRolled) {
+#pragma unroll 1
+        for (int i = n - 1; i >= 0; --i) step2(i, taur[i]);
+    } else {
+        for (int i0 = ((n - 1) / 4) * 4; i0 >= 0; i0 -= 4) {
+            const Chunk<T> ct = ld_chunk<T, VEC>(taur, i0, n);
+#pragma unroll
+            for (int j = 3; j >= 0; --j)
+                if (VEC || i0 + j < n) step2(i0 + j, ct.v[j]);
         }
     }
 
     // ---- sweep 3: lambda and qdd
     V3<Z> lv = mk3(Z(0), Z(0), Z(0)), lw = mk3(Z(0), Z(0), Z(0));
-    for (int kc = 0; kc < nchunks; ++kc) {
-        const int i0 = 4 * kc;
-        Chunk<T> out;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = i0 + j;
-            out.v[j] = T(0);
-            if (VEC || i < n) {
-                const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
-                DhRot<Z> R;
-                V3<Z> bi;
-                if constexpr (sizeof(Z) == 8) {
-                    const double *ri = sd + i * kAbaDh64;
-                    R = dh_rot(ri[0], ri[1], (double)c, (double)s);
-                    bi = mk3(ri[2], ri[3], ri[4]);
-                } else {
-                    const T *Lt = sc + i * kDhConsts;
-                    R = dh_rot((Z)Lt[0], (Z)Lt[1], (Z)c, (Z)s);
-                    bi = mk3((Z)Lt[2], (Z)Lt[3], (Z)Lt[4]);
-                }
-                // a = Ad_{f^-1} lambda
-                V3<Z> av = dh_mulT(R, cross_add(lw, bi, lv)), aw = dh_mulT(R, lw);
-                const V3<Z> uv = mk3(aba_zget(wsz, B, b, i, 0), aba_zget(wsz, B, b, i, 1), aba_zget(wsz, B, b, i, 2));
-                const V3<Z> uw = mk3(aba_zget(wsz, B, b, i, 3), aba_zget(wsz, B, b, i, 4), aba_zget(wsz, B, b, i, 5));
-                const Z ch = aba_zget(wsz, B, b, i, 6), iom = aba_zget(wsz, B, b, i, 7);
-                const double ua = (double)uv.x * av.x + (double)uv.y * av.y + (double)uv.z * av.z +
-                                  (double)uw.x * aw.x + (double)uw.y * aw.y + (double)uw.z * aw.z;
-                const double qdd_i = (double)ch - (double)iom * ua;
-                aw.z += (Z)qdd_i;
-                lv = av;
-                lw = aw;
-                out.v[j] = (T)qdd_i;
-                if (!(qdd_i == qdd_i)) bad = 1;
-            }
+    // one link of the sweep; returns qdd_i
+    auto step3 = [&](int i) -> T {
+        const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
+        DhRot<Z> R;
+        V3<Z> bi;
+        if constexpr (kZrec) {
+            const D *ri = sd + i * kAbaDh64;
+            R = dh_rot(ri[0], ri[1], dcvt<D>(c), dcvt<D>(s));
+            bi = mk3(ri[2], ri[3], ri[4]);
+        } else {
+            const T *Lt = sc + i * kDhConsts;
+            R = dh_rot(dcvt<Z>(Lt[0]), dcvt<Z>(Lt[1]), dcvt<Z>(c), dcvt<Z>(s));
+            bi = mk3(dcvt<Z>(Lt[2]), dcvt<Z>(Lt[3]), dcvt<Z>(Lt[4]));
         }
-        st_chunk<T, VEC>(qddr, i0, n, out);
+        // a = Ad_{f^-1} lambda
+        V3<Z> av = dh_mulT(R, cross_add(lw, bi, lv)), aw = dh_mulT(R, lw);
+        const V3<Z> uv = mk3(aba_zget(wsz, B, b, i, 0), aba_zget(wsz, B, b, i, 1), aba_zget(wsz, B, b, i, 2));
+        const V3<Z> uw = mk3(aba_zget(wsz, B, b, i, 3), aba_zget(wsz, B, b, i, 4), aba_zget(wsz, B, b, i, 5));
+        const Z ch = aba_zget(wsz, B, b, i, 6), iom = aba_zget(wsz, B, b, i, 7);
+        D ua = dcvt<D>(uv.x) * dcvt<D>(av.x);
+        ua = fma(dcvt<D>(uv.y), dcvt<D>(av.y), ua);
+        ua = fma(dcvt<D>(uv.z), dcvt<D>(av.z), ua);
+        ua = fma(dcvt<D>(uw.x), dcvt<D>(aw.x), ua);
+        ua = fma(dcvt<D>(uw.y), dcvt<D>(aw.y), ua);
+        ua = fma(dcvt<D>(uw.z), dcvt<D>(aw.z), ua);
+        const D qdd_i = dcvt<D>(ch) - dcvt<D>(iom) * ua;
+        aw.z = aw.z + dcvt<Z>(qdd_i);
+        lv = av;
+        lw = aw;
+        if (disnan(qdd_i)) bad = 1;
+        return dcvt<T>(qdd_i);
+    };
+    if constexpr (kRolled) {
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) qddr[i] = step3(i);
+    } else {
+        for (int kc = 0; kc < nchunks; ++kc) {
+            const int i0 = 4 * kc;
+            Chunk<T> out;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) out.v[j] = (VEC || i0 + j < n) ? step3(i0 + j) : T(0);
+            st_chunk<T, VEC>(qddr, i0, n, out);
+        }
     }
     return bad;
 }
 
-template <typename T, typename Z, int NMAX, int BLOCK, int TRIG>
-__global__ void __launch_bounds__(BLOCK)
-aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
+template <typename T, typename D, typename Z, int NMAX, int BLOCK, int TRIG>
+__global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
+aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, D, NMAX> pc, int n, int B,
               const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
               T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
               Z *__restrict__ wsz, BaseParams<T> base)
@@ -316,8 +352,9 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, NMAX> pc, int n, int B,
     const int b = blockIdx.x * BLOCK + threadIdx.x;
     if (b >= B) return;
     const size_t row = (size_t)b * (size_t)n;
-    const int bad = aba_dh_instance<T, Z, TRIG, true>(pc.c, pc.d, n, q + row, qd + row, tau + row,
-                                                      qdd_out + row, ws, wsz, B, b, base);
+    const int bad = aba_dh_instance<T, D, Z, TRIG, true>(pc.c, pc.d, n, q + row, qd + row,
+                                                         tau + row, qdd_out + row, ws, wsz, B, b,
+                                                         base);
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }
 

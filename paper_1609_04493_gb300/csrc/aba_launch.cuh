@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <type_traits>
 
 #include "aba.cuh"
 #include "aba_dh.cuh"
@@ -61,7 +62,7 @@ int launch_aba_k(const rd_model *m, int B, const void *q, const void *qd, const 
     return RD_OK;
 }
 
-template <typename T, typename Z, int NMAX, int TRIG>
+template <typename T, typename D, typename Z, int NMAX, int TRIG>
 int launch_aba_dh_k(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                     void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
 {
@@ -75,15 +76,18 @@ int launch_aba_dh_k(const rd_model *m, int B, const void *q, const void *qd, con
         bp.dV0[k] = (T)bb[6 + k];
         bp.Fn[k] = (T)bb[12 + k];
     }
-    AbaDhConsts<T, NMAX> pc;
+    AbaDhConsts<T, D, NMAX> pc;
     for (int k = 0; k < NMAX * kDhConsts; ++k)
         pc.c[k] = k < n * kDhConsts ? (T)m->host_dh64[k] : T(0);
-    for (int k = 0; k < NMAX * kAbaDh64; ++k)
-        pc.d[k] = k < n * kAbaDh64 ? m->host_aba64[k] : 0.0;
+    for (int k = 0; k < NMAX * kAbaDh64; ++k) {
+        const double v = k < n * kAbaDh64 ? m->host_aba64[k] : 0.0;
+        if constexpr (std::is_same<D, double>::value) pc.d[k] = v;
+        else pc.d[k] = df_split_host(v);
+    }
     const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
     Z *wsz = reinterpret_cast<Z *>(static_cast<char *>(ws) + ((a + 255) & ~(size_t)255));
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
-    aba_dh_kernel<T, Z, NMAX, BLOCK, TRIG><<<grid, BLOCK, 0, stream>>>(
+    aba_dh_kernel<T, D, Z, NMAX, BLOCK, TRIG><<<grid, BLOCK, 0, stream>>>(
         pc, n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
         static_cast<const T *>(tau), static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz, bp);
     cudaError_t e = cudaGetLastError();
@@ -91,13 +95,13 @@ int launch_aba_dh_k(const rd_model *m, int B, const void *q, const void *qd, con
     return RD_OK;
 }
 
-template <typename T, typename Z>
+template <typename T, typename D, typename Z>
 int launch_aba_dh(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                   void *qdd, int *status, void *ws, const double *base18, cudaStream_t s)
 {
     if (m->n <= 32)
-        return launch_aba_dh_k<T, Z, 32, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
-    return launch_aba_dh_k<T, Z, 64, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+        return launch_aba_dh_k<T, D, Z, 32, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    return launch_aba_dh_k<T, D, Z, 64, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
 
 template <typename T>
@@ -116,10 +120,14 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
     if (vec && m->n <= 64 && !(flags & RD_ABA_JOINT_FRAMES)) {
         // common-normal frames, constants as a kernel parameter (aba_dh.cuh)
         if constexpr (sizeof(T) == 4) {
+            if (!(flags & RD_ABA_FP64_UPDATE))
+                return fp32_scans
+                           ? launch_aba_dh<T, DF, T>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+                           : launch_aba_dh<T, DF, DF>(m, B, q, qd, tau, qdd, status, ws, base18, s);
             if (fp32_scans)
-                return launch_aba_dh<T, T>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+                return launch_aba_dh<T, double, T>(m, B, q, qd, tau, qdd, status, ws, base18, s);
         }
-        return launch_aba_dh<T, double>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+        return launch_aba_dh<T, double, double>(m, B, q, qd, tau, qdd, status, ws, base18, s);
     }
     if constexpr (sizeof(T) == 4) {
         if (fp32_scans)

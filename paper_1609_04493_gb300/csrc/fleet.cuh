@@ -7,9 +7,10 @@
 // sit at [off_r, off_r + n_r) of every data array. One thread evaluates one
 // request with the per-instance bodies of the single-chain kernels (the
 // re-derive-in-the-backward-sweep RNEA, and the articulated-body algorithm
-// with FP64 inertia updates and solves) in the common-normal frames of
-// spatial_dh.cuh, reading its robot's constants from global memory since no
-// two requests need share them.
+// with its inertia updates and solves in double-float arithmetic for FP32
+// data, FP64 for FP64 data) in the common-normal frames of spatial_dh.cuh,
+// reading its robot's constants from global memory since no two requests need
+// share them.
 //
 // Scheduling: the host sorts requests (forward dynamics first, then by
 // decreasing n) so that the 32 requests a warp takes are alike.
@@ -20,15 +21,21 @@
 //   per-group:  one ordinary launch per run of equal (kind, n) in the sorted
 //               order -- the "one launch per request size" comparison.
 #pragma once
+#include <type_traits>
+
 #include "aba_dh.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
 
+// scalar of the forward-dynamics inertia updates and solves for data type T
+template <typename T>
+using FleetUpdate = typename std::conditional<sizeof(T) == 4, DF, double>::type;
+
 template <typename T>
 struct FleetArgs {
     const T *consts;          // [total links][16] common-normal constants
-    const double *consts64;   // [total links][32] FP64 forward-dynamics records
+    const FleetUpdate<T> *records;  // [total links][32] forward-dynamics records
     const int *robot_n;       // [robots]
     const int *robot_link;    // [robots] first constant row
     const T *robot_gb;        // [robots][12] base frame D_{-1} in frame 0: R (9), p (3)
@@ -131,12 +138,14 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int r)
     if (a.req_kind[r] == 0) {
         rnea_dh_instance<T, kTrigPoly>(sc, n, a.q + off, a.qd + off, a.in2 + off, a.out + off, bp);
     } else {
+        using D = FleetUpdate<T>;
+        static_assert(sizeof(D) == sizeof(double), "solve-state slots are 8 bytes");
         unsigned char *w = a.ws + a.req_ws[r];
         T *wt = reinterpret_cast<T *>(w);
-        double *wz = reinterpret_cast<double *>(
+        D *wz = reinterpret_cast<D *>(
             w + (((size_t)n * kAbaStateScalars * sizeof(T) + 15) & ~(size_t)15));
-        const int bad = aba_dh_instance<T, double, kTrigPoly, false>(
-            sc, a.consts64 + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off, a.out + off,
+        const int bad = aba_dh_instance<T, D, D, kTrigPoly, false>(
+            sc, a.records + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off, a.out + off,
             wt, wz, 1, 0, bp);
         if (a.status) a.status[r] = bad ? 1 : 0;
     }

@@ -21,6 +21,7 @@ struct rd_fleet {
     float *c32 = nullptr;     // [links][16] common-normal constants
     double *c64 = nullptr;    // same in FP64
     double *aba64 = nullptr;  // [links][32] FP64 forward-dynamics records
+    rdyn::DF *abadf = nullptr;  // the same split into double-float pairs (FP32 data)
     int *robot_n = nullptr, *robot_link = nullptr;
     float *gb32 = nullptr, *tn32 = nullptr;  // [robots][12] boundary frames
     double *gb64 = nullptr, *tn64 = nullptr;
@@ -62,6 +63,7 @@ extern "C" void rd_fleet_destroy(rd_fleet *f)
     cudaFree(f->c32);
     cudaFree(f->c64);
     cudaFree(f->aba64);
+    cudaFree(f->abadf);
     cudaFree(f->robot_n);
     cudaFree(f->robot_link);
     cudaFree(f->gb32);
@@ -122,7 +124,10 @@ extern "C" int rd_fleet_create(int nrobots, const int *n, const double *M, const
     std::vector<float> tn32(tn.begin(), tn.end()), gb32(gb.begin(), gb.end());
     if (e == cudaSuccess) e = upload(&f->c64, all64.data(), all64.size());
     if (e == cudaSuccess) e = upload(&f->c32, all32.data(), all32.size());
+    std::vector<rdyn::DF> alldf(allaba.size());
+    for (size_t k = 0; k < allaba.size(); ++k) alldf[k] = rdyn::df_split_host(allaba[k]);
     if (e == cudaSuccess) e = upload(&f->aba64, allaba.data(), allaba.size());
+    if (e == cudaSuccess) e = upload(&f->abadf, alldf.data(), alldf.size());
     if (e == cudaSuccess) e = upload(&f->robot_n, n, (size_t)nrobots);
     if (e == cudaSuccess) e = upload(&f->robot_link, link.data(), link.size());
     if (e == cudaSuccess) e = upload(&f->tn64, tn.data(), tn.size());
@@ -249,12 +254,13 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
         a.consts = f->c32;
         a.robot_tn = f->tn32;
         a.robot_gb = f->gb32;
+        a.records = f->abadf;
     } else {
         a.consts = f->c64;
         a.robot_tn = f->tn64;
         a.robot_gb = f->gb64;
+        a.records = f->aba64;
     }
-    a.consts64 = f->aba64;
     a.robot_n = f->robot_n;
     a.robot_link = f->robot_link;
     a.order = p->order;

@@ -3,8 +3,9 @@ against the FP64 oracle's ABA and JSIIA, through the C ABI; round trip
 ID(FD(tau)) = tau.
 
 Metric: per instance max_i |qdd - qdd*| / max_i |qdd*|, max over the batch.
-Bars: FP32 (scans in FP32, inertia update and Omega solves in FP64) 1e-3;
-FP64 1e-8 (FD amplifies rounding by the conditioning of M(q)).
+Bars: FP32 data 1e-3 (inertia update and Omega solves in double-float
+arithmetic by default, or FP64); FP64 1e-8 (FD amplifies rounding by the
+conditioning of M(q)).
 """
 import numpy as np
 import pytest
@@ -174,6 +175,74 @@ def test_aba_common_normal_flags_a_singular_joint(cuda_lib):
     ch.inertia[3] = [1.0, 0.0, 0.0, 0.2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]
     model = cuda_lib.Model(ch)
     x = torch.zeros((6, 4), dtype=torch.float64, device="cuda")
+    status = torch.full((6,), -7, dtype=torch.int32, device="cuda")
+    cuda_lib.aba(model, x, x, x + 1.0, status=status)
+    assert torch.all(status == 1)
+
+
+# ---- FP32 data: double-float (default) and FP64 (RD_ABA_FP64_UPDATE) inertia
+# updates and solves in the common-normal kernel
+
+@pytest.mark.parametrize("n", [4, 8, 32, 48, 64])
+def test_aba_fp64_update_matches_oracle(cuda_lib, n):
+    qdd, ch, h, _ = run(cuda_lib, n, 300, "float32", seed=41, flags=cuda_lib.RD_ABA_FP64_UPDATE)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    assert oracle.rel_err(qdd, ref) <= TOL["float32"], f"n={n}"
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_aba_double_float_agrees_with_fp64_update(cuda_lib, n):
+    """The double-float and FP64 inertia updates differ by a few units of 2^-48
+    relative per operation, far below the FP32 rounding of qdd: the two FP32
+    outputs agree to a few FP32 ulps."""
+    a, _, _, _ = run(cuda_lib, n, 512, "float32", seed=47, flags=cuda_lib.RD_ABA_FP64_UPDATE)
+    b, _, _, _ = run(cuda_lib, n, 512, "float32", seed=47)
+    assert oracle.rel_err(a, b) <= 1e-5
+
+
+def test_aba_fp64_update_full_batch_sampled(cuda_lib):
+    """B = 16384, n = 64 with the FP64 update: the bars of
+    test_aba_full_batch_sampled (which runs the double-float default)."""
+    n = 64
+    qdd, ch, h, _ = run(cuda_lib, n, 16384, "float32", seed=1609,
+                        flags=cuda_lib.RD_ABA_FP64_UPDATE)
+    idx = np.arange(0, 16384, 32)
+    ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
+    assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
+    back = oracle.rnea(ch, h["q"][idx], h["qd"][idx], qdd[idx])
+    bias = oracle.rnea(ch, h["q"][idx], h["qd"][idx], np.zeros_like(qdd[idx]))
+    scale = np.maximum(np.max(np.abs(h["tau"][idx]), axis=1), np.max(np.abs(bias), axis=1))
+    err = np.max(np.abs(back - h["tau"][idx]), axis=1) / scale
+    assert err.max() <= 1e-4 * n / 16, err.max()
+
+
+def test_aba_fp64_update_with_fp32_scans(cuda_lib):
+    flags = cuda_lib.RD_ABA_FP64_UPDATE | cuda_lib.RD_ABA_SCANS_IN_DTYPE
+    qdd, ch, h, _ = run(cuda_lib, 16, 300, "float32", seed=53, flags=flags)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    assert oracle.rel_err(qdd, ref) <= TOL["float32"]
+
+
+@pytest.mark.parametrize("fp64_update", [False, True])
+def test_aba_fp32_base_motion_and_wrench(cuda_lib, fp64_update):
+    flags = cuda_lib.RD_ABA_FP64_UPDATE if fp64_update else 0
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    qdd, ch, h, _ = run(cuda_lib, 12, 90, "float32", base=base, flags=flags)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=base)
+    assert oracle.rel_err(qdd, ref) <= TOL["float32"]
+
+
+def test_aba_double_float_flags_a_singular_joint(cuda_lib):
+    """The exact Omega_n = 0 of test_aba_common_normal_flags_a_singular_joint,
+    in FP32 data with the double-float solves."""
+    import torch
+
+    ch = chaingen.make_chain(4, seed=5)
+    ch.S[3] = [0.0, 0.0, 0.0, 0.0, 0.0, 1.0]
+    ch.inertia[3] = [1.0, 0.0, 0.0, 0.2, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    model = cuda_lib.Model(ch)
+    x = torch.zeros((6, 4), dtype=torch.float32, device="cuda")
     status = torch.full((6,), -7, dtype=torch.int32, device="cuda")
     cuda_lib.aba(model, x, x, x + 1.0, status=status)
     assert torch.all(status == 1)
