@@ -91,6 +91,10 @@ FD_EXEC_FLOP64_PER_LINK = 400
 # the FMA-pipe count of an ncu capture at n = 64, B = 16384 (105.4 M warp
 # instructions, 94% of all)
 FD_DF_EXEC_FP32_INST_PER_LINK = 3217
+# FP32-pipe instructions per link of the double-float kernel for FP64 data
+# (RD_VARIANT_SERIAL_DF), from the FMA-pipe count of an ncu capture at n = 32,
+# B = 65536 (166.2 M warp instructions, 92% of all)
+RNEA_DF_EXEC_FP32_INST_PER_LINK = 2535
 # bytes an inverse-dynamics link of the uneven workload moves: q, qd, qdd, tau
 # (16) plus its robot's constants streamed per request (112)
 UNEVEN_ID_BYTES_PER_LINK = 128
@@ -108,9 +112,11 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
-    p.add_argument("--kernel-only", choices=["f32", "f64", "vjp", "aba", "fleet"], default=None,
+    p.add_argument("--kernel-only", choices=["f32", "f64", "f64df", "vjp", "aba", "fleet"],
+                   default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
-                        "(f32/f64: RNEA n=32 B=65536; vjp: adjoint n=32 B=8192; "
+                        "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
+                        "arithmetic; vjp: adjoint n=32 B=8192; "
                         "aba: forward dynamics n=64 B=16384; fleet: 20000 mixed requests)")
     return p.parse_args()
 
@@ -544,7 +550,33 @@ def run_ours(args):
                        "algorithmic_tflops": fp64_flops,
                        "algorithmic_frac_of_nominal": fp64_flops / FP64_NOMINAL_TFLOPS,
                        "fp32_over_fp64": value / (world * BATCH * K64 / t64)}
-        del g64, gw64, sets64
+        # the same FP64 data in double-float arithmetic on the FP32 pipe
+        vdf = rd.RD_VARIANT_SERIAL_DF
+        gwdf = capture(torch, rd, model, sets64, 3, variant=vdf)
+        gwdf.replay()
+        torch.cuda.synchronize()
+        gdf = capture(torch, rd, model, sets64, K64, variant=vdf)
+        tdf = max_over_ranks(dist, timed_graph(torch, gdf, dist, sampler))
+        x0 = sets64[0]
+        ref64 = rd.rnea(model, x0["q"], x0["qd"], x0["qdd"])
+        got = rd.rnea(model, x0["q"], x0["qd"], x0["qdd"], variant=vdf)
+        scale = ref64.abs().amax(dim=1).clamp_min(1e-300)
+        diff = float(((got - ref64).abs().amax(dim=1) / scale).max())
+        t_issue = N_LINKS * BATCH * RNEA_DF_EXEC_FP32_INST_PER_LINK / (
+            SM_COUNT * FP32_LANES_PER_SM * 2.070e9)
+        t_floor = N_LINKS * BATCH * JOINT_FRAME_FLOP_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12)
+        res["fp64"]["double_float"] = {
+            "value": world * BATCH * K64 / tdf, "unit": UNIT, "steps": K64,
+            "ms_per_step": tdf / K64 * 1e3, "variant": "RD_VARIANT_SERIAL_DF",
+            "fp32_inst_per_link": RNEA_DF_EXEC_FP32_INST_PER_LINK,
+            "roofline_ms": t_issue * 1e3, "roofline_frac": t_issue / (tdf / K64),
+            "fp64_pipe_floor_ms": t_floor * 1e3,
+            "max_rel_diff_vs_fp64": diff,
+            "roofline": ("FP32-pipe issue time of the kernel's FP32 instructions per link at "
+                         f"{SM_COUNT} x {FP32_LANES_PER_SM} lanes x 2.07 GHz over the measured "
+                         "time; fp64_pipe_floor_ms: the FP64 kernel's executed "
+                         f"{JOINT_FRAME_FLOP_PER_LINK} flop per link at the nominal FP64 peak")}
+        del g64, gw64, gdf, gwdf, sets64
 
         # ---- end to end through the host-array entry point
         st = chaingen.make_states(BATCH, N_LINKS, seed=3000 + rank)
@@ -665,12 +697,13 @@ def run_kernel_only(args):
     rd.load()
     dev = torch.device("cuda", 0)
     calls = args.warmup + args.steps
-    if args.kernel_only in ("f32", "f64"):
+    if args.kernel_only in ("f32", "f64", "f64df"):
         dt = torch.float32 if args.kernel_only == "f32" else torch.float64
+        v = rd.RD_VARIANT_SERIAL_DF if args.kernel_only == "f64df" else rd.RD_VARIANT_AUTO
         model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
         x = make_inputs(torch, dev, dt, 1, 1000)[0]
         for _ in range(calls):
-            rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"])
+            rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"], variant=v)
         res = x["tau"]
     elif args.kernel_only == "vjp":
         model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))

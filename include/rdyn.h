@@ -97,10 +97,20 @@ enum rd_variant {
                                  keeps its state in shared memory. AUTO takes this kernel for
                                  FP32 batches of more than 2048 whole-chunk rows. */
     RD_VARIANT_SERIAL_DH_RECOMPUTE = 7, /* as 6 with K = 0 (no full state) */
-    RD_VARIANT_SERIAL_DH_TMEM = 8 /* as 6 (FP32, n <= 32, n % 4 == 0, aligned rows) with the
-                                     state of the first 16 links in tensor memory: blocks of
-                                     128 threads, four per SM, each owning 128 TMEM columns;
-                                     K by RD_TUNE_STORED_LINKS (0 = largest that fits) */
+    RD_VARIANT_SERIAL_DH_TMEM = 8, /* as 6 (FP32, n <= 32, n % 4 == 0, aligned rows) with the
+                                      state of the first 16 links in tensor memory: blocks of
+                                      128 threads, four per SM, each owning 128 TMEM columns;
+                                      K by RD_TUNE_STORED_LINKS (0 = largest that fits) */
+    RD_VARIANT_SERIAL_DF = 9 /* RD_F64 data only, n <= 64, rows of any alignment: one thread
+                                per instance in common-normal frames with every value a
+                                double-float pair (two FP32 numbers, about 48 significand
+                                bits; Dekker 1971) on the FP32 pipe instead of FP64; cos/sin
+                                of q_i (sin/cos by Cody-Waite reduction and Taylor series,
+                                see rd_joint_trig_df) kept in shared memory, motion
+                                re-derived in the backward sweep. Relative error a few units
+                                of 2^-48 per operation, for values within the FP32 exponent
+                                range (magnitudes about 1e-38 to 3e38). Never chosen by
+                                AUTO. */
 };
 /* Lane-parallel scan: L lanes of one warp per instance, L in {2,4,8,16,32};
  * each lane owns ceil(n/L) consecutive links, lanes combine their segments
@@ -390,6 +400,17 @@ int rd_measure_fma_peak(int dtype, double *tflops, void *stream);
  * Errors: RD_ERR_RANGE (count < 0), RD_ERR_ARG (null pointer), RD_ERR_CUDA.
  */
 int rd_joint_trig(int flags, const float *x, float *s, float *c, int count, void *stream);
+
+/*
+ * rd_joint_trig_df -- diagnostic, outside the paper's method: the sine and
+ * cosine that RD_VARIANT_SERIAL_DF evaluates for each FP64 joint angle, in
+ * double-float arithmetic (Cody-Waite reduction by pi/2 in FP64, Taylor series
+ * with inverse-factorial coefficients), returned as doubles (hi + lo).
+ *   x, s, c  device double[count]: angles in radians in, sin and cos out.
+ *   stream   cudaStream_t. Asynchronous; never allocates.
+ * Errors: RD_ERR_RANGE (count < 0), RD_ERR_ARG (null pointer), RD_ERR_CUDA.
+ */
+int rd_joint_trig_df(const double *x, double *s, double *c, int count, void *stream);
 
 /*
  * rd_rnea_last_config -- the kernel the calling thread's last rnea_batch call

@@ -21,6 +21,7 @@ RD_VARIANT_SERIAL_HYBRID = 5
 RD_VARIANT_SERIAL_DH = 6
 RD_VARIANT_SERIAL_DH_RECOMPUTE = 7
 RD_VARIANT_SERIAL_DH_TMEM = 8
+RD_VARIANT_SERIAL_DF = 9
 
 
 RD_FLAG_FAST_TRIG = 0x1000
@@ -123,6 +124,8 @@ def load(build_if_missing=True):
         lib.rd_measure_fma_peak.restype = I
         lib.rd_joint_trig.argtypes = [I, P, P, P, I, P]
         lib.rd_joint_trig.restype = I
+        lib.rd_joint_trig_df.argtypes = [P, P, P, I, P]
+        lib.rd_joint_trig_df.restype = I
         IP = ctypes.POINTER(ctypes.c_int)
         lib.rd_rnea_last_config.argtypes = [IP, IP, IP]
         lib.rd_rnea_last_config.restype = I
@@ -175,6 +178,21 @@ def joint_trig(x, fast=False, stream=None):
     st = stream or torch.cuda.current_stream(x.device)
     _check(lib.rd_joint_trig(RD_FLAG_FAST_TRIG if fast else 0, x.data_ptr(), s.data_ptr(),
                              c.data_ptr(), x.numel(), ctypes.c_void_p(st.cuda_stream)))
+    return s, c
+
+
+def joint_trig_df(x, stream=None):
+    """(sin x, cos x) as the double-float kernel of FP64 data evaluates them
+    (rd_joint_trig_df; diagnostic). x: contiguous float64 CUDA tensor."""
+    import torch
+
+    lib = load()
+    if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("joint_trig_df expects a contiguous float64 CUDA tensor")
+    s, c = torch.empty_like(x), torch.empty_like(x)
+    st = stream or torch.cuda.current_stream(x.device)
+    _check(lib.rd_joint_trig_df(x.data_ptr(), s.data_ptr(), c.data_ptr(), x.numel(),
+                                ctypes.c_void_p(st.cuda_stream)))
     return s, c
 
 

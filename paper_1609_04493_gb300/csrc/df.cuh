@@ -74,6 +74,7 @@ __device__ __forceinline__ DF fma(DF x, DF y, DF z)
 }
 
 __device__ __forceinline__ DF &operator+=(DF &x, DF y) { return x = x + y; }
+__device__ __forceinline__ DF &operator-=(DF &x, DF y) { return x = x - y; }
 
 }  // namespace dfloat
 using dfloat::DF;
@@ -150,11 +151,20 @@ __device__ __forceinline__ To dcvt(From x)
     return DCvt<To>::from(x);
 }
 
-// nearest double-float of a double (host side: records are split once)
-inline DF df_split_host(double v)
+// nearest double-float of a double (host side: records are split once;
+// constexpr, so constant tables split at compile time)
+constexpr DF df_split_host(double v)
 {
-    const float hi = (float)v;
-    return DF(hi, (float)(v - (double)hi));
+    return DF((float)v, (float)(v - (double)(float)v));
 }
+
+// double <-> double-float on the device (conversions on the FP64 path)
+__device__ __forceinline__ DF df_from_double(double v)
+{
+    const float hi = __double2float_rn(v);
+    return DF(hi, __double2float_rn(v - (double)hi));
+}
+
+__device__ __forceinline__ double df_to_double(DF x) { return (double)x.hi + (double)x.lo; }
 
 }  // namespace rdyn

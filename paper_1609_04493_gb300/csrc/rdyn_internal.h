@@ -62,6 +62,11 @@ int rd_rnea_dh_f32(const rd_model *m, int B, const void *q, const void *qd, cons
 int rd_rnea_dh_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
                    int kfull, int tmem, cudaStream_t s);
+// FP64 data in double-float arithmetic (RD_VARIANT_SERIAL_DF), n <= 64
+int rd_rnea_df_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                   void *tau, const double *base18, int block, cudaStream_t s);
+// the double-float sine and cosine of the FP64 kernels, as doubles (rd_joint_trig_df)
+int rd_df_trig_launch(const double *x, double *s, double *c, int count, cudaStream_t stream);
 int rd_rnea_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
                          const void *qdd, void *tau, const double *base18, int variant,
                          cudaStream_t s);

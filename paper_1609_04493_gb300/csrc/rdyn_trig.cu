@@ -38,3 +38,12 @@ extern "C" int rd_joint_trig(int flags, const float *x, float *s, float *c, int 
     if (e != cudaSuccess) return rd_cuda_fail(e, "rd_joint_trig launch");
     return RD_OK;
 }
+
+extern "C" int rd_joint_trig_df(const double *x, double *s, double *c, int count, void *stream)
+{
+    g_rd_error.clear();
+    if (count < 0) return rd_fail(RD_ERR_RANGE, "rd_joint_trig_df: count %d < 0", count);
+    if (count == 0) return RD_OK;
+    if (!x || !s || !c) return rd_fail(RD_ERR_ARG, "rd_joint_trig_df: null pointer");
+    return rd_df_trig_launch(x, s, c, count, static_cast<cudaStream_t>(stream));
+}

@@ -372,6 +372,12 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         else
             return rd_rnea_dh_f64(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, tmem, s);
     }
+    if (variant == RD_VARIANT_SERIAL_DF) {
+        if constexpr (sizeof(T) == 8)
+            return rd_rnea_df_f64(m, B, q, qd, qdd, tau, base18, block, s);
+        else
+            return rd_fail(RD_ERR_DTYPE, "rnea_batch: RD_VARIANT_SERIAL_DF takes RD_F64 data");
+    }
     if (variant == RD_VARIANT_SERIAL_HYBRID) {
         if (!block) block = 32;
         const int K = reglinks ? reglinks : 16;
