@@ -112,11 +112,12 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
-    p.add_argument("--kernel-only", choices=["f32", "f64", "f64df", "vjp", "aba", "fleet"],
+    p.add_argument("--kernel-only", choices=["f32", "f64", "f64df", "host", "vjp", "aba", "fleet"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
-                        "arithmetic; vjp: adjoint n=32 B=8192; "
+                        "arithmetic; host: rnea_batch_host on pinned FP32 arrays, the same "
+                        "size; vjp: adjoint n=32 B=8192; "
                         "aba: forward dynamics n=64 B=16384; fleet: 20000 mixed requests)")
     return p.parse_args()
 
@@ -597,8 +598,22 @@ def run_ours(args):
         res["e2e"] = {"value": world * BATCH * Ke / te, "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
                       "d2h_bytes_per_step": BATCH * N_LINKS * 4,
-                      "api": "rnea_batch_host, pinned host arrays, FP32 (row chunks "
-                             "pipelined: copies in, kernel, copies out on three streams)"}
+                      "api": "rnea_batch_host, pinned host arrays, FP32: the kernel reads "
+                             "the rows from host memory and writes tau back itself (16-byte "
+                             "slab transfers; RD_RNEA_KERNEL_DH_HOST)"}
+        # the staged path on the same arrays: copy engines, row chunks pipelined
+        # over three streams
+        for _ in range(3):
+            rd.rnea_host(model, *host, out=out, variant=rd.RD_FLAG_HOST_COPY)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            rd.rnea_host(model, *host, out=out, variant=rd.RD_FLAG_HOST_COPY)
+        ts = max_over_ranks(dist, time.perf_counter() - t0)
+        res["e2e"]["staged_copies"] = {"value": world * BATCH * Ke / ts, "unit": UNIT,
+                                       "ms_per_step": ts / Ke * 1e3}
+        link_bytes = 4 * BATCH * N_LINKS * 4
+        res["e2e"]["link_gbs"] = link_bytes / (te / Ke) / 1e9
 
         # ---- adjoint (rnea_vjp), n = 32 FP32
         res["adjoint"] = adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K)
@@ -705,6 +720,13 @@ def run_kernel_only(args):
         for _ in range(calls):
             rd.rnea(model, x["q"], x["qd"], x["qdd"], out=x["tau"], variant=v)
         res = x["tau"]
+    elif args.kernel_only == "host":
+        model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
+        st = chaingen.make_states(BATCH, N_LINKS, seed=3000)
+        host = [torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("q", "qd", "qdd")]
+        res = torch.empty_like(host[0]).pin_memory()
+        for _ in range(calls):
+            rd.rnea_host(model, *host, out=res)
     elif args.kernel_only == "vjp":
         model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
         st = chaingen.make_states(8192, N_LINKS, seed=5000, kinds=("q", "qd", "qdd", "w"))

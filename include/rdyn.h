@@ -123,6 +123,9 @@ enum rd_variant {
  * common-normal-frame kernels. Faster; the torque error can then exceed 1e-4
  * of max|tau| on instances whose torques nearly cancel. */
 #define RD_FLAG_FAST_TRIG 0x1000
+/* OR-able flag for rnea_batch_host: stage the arrays through device buffers
+ * with the copy engines even where the kernel could read them in place. */
+#define RD_FLAG_HOST_COPY 0x4000
 /* OR-able tuning field: threads per block of the one-thread-per-instance
  * kernels (32, 64 or 128; 0 = library default). */
 #define RD_TUNE_BLOCK(threads) ((threads) == 32 ? (5 << 16) : (threads) == 64 ? (6 << 16) \
@@ -189,15 +192,22 @@ int rnea_batch(const rd_model *model, int B, int dtype, const void *q, const voi
 
 /*
  * rnea_batch_host -- rnea_batch on HOST arrays; returns when tau is on the host.
- * q, qd, qdd are copied into device buffers owned by the model (grown on
- * demand: only this path may allocate device memory; rnea_batch never does),
- * the kernel runs, and tau is copied back. Large batches are split into row
- * chunks pipelined over three streams (copies in, kernels on the caller's
- * stream, copies out), so the inbound copies of a chunk overlap the kernel of
- * the one before. Chunks are never smaller than the batch size at which AUTO
- * switches kernels, so tau is identical to rnea_batch on the same rows. Pinned
- * host memory copies at full link speed (~200 GB/s per direction on GB300).
- * Same argument meaning as rnea_batch.
+ * In place: with variant RD_VARIANT_AUTO, RD_F32 data, n % 4 == 0, n <= 64 and
+ * all four arrays mapped pinned host memory (cudaHostAlloc under unified
+ * addressing, as pinned torch tensors are) on 16-byte boundaries, one kernel
+ * reads the rows from host memory and writes tau back itself, each block moving
+ * contiguous slabs (RD_RNEA_KERNEL_DH_HOST; the same recursion as rnea_batch in
+ * another schedule, so tau agrees with it to FP32 rounding).
+ * Staged otherwise, or with variant | RD_FLAG_HOST_COPY: q, qd, qdd are copied
+ * into device buffers owned by the model (grown on demand: only this path may
+ * allocate device memory; rnea_batch never does), the kernel runs, and tau is
+ * copied back. Large batches are split into row chunks pipelined over three
+ * streams (copies in, kernels on the caller's stream, copies out), so the
+ * inbound copies of a chunk overlap the kernel of the one before. Chunks are
+ * never smaller than the batch size at which AUTO switches kernels, so tau is
+ * identical to rnea_batch on the same rows. Pinned host memory copies at full
+ * link speed (~200 GB/s per direction on GB300).
+ * Same argument meaning as rnea_batch; RD_ERR_ARG also when tau aliases an input.
  */
 int rnea_batch_host(rd_model *model, int B, int dtype, const void *q, const void *qd,
                     const void *qdd, void *tau, const double *base, int variant,
@@ -428,6 +438,7 @@ int rd_joint_trig_df(const double *x, double *s, double *c, int count, void *str
  */
 #define RD_RNEA_KERNEL_DH_PARAM 0x206
 #define RD_RNEA_KERNEL_DH_TMEM 0x208
+#define RD_RNEA_KERNEL_DH_HOST 0x209 /* rnea_batch_host reading mapped host arrays */
 int rd_rnea_last_config(int *kernel, int *block, int *stored_links);
 
 /* Message for the last error on the calling thread ("" if none). */

@@ -22,6 +22,8 @@ RD_VARIANT_SERIAL_DH = 6
 RD_VARIANT_SERIAL_DH_RECOMPUTE = 7
 RD_VARIANT_SERIAL_DH_TMEM = 8
 RD_VARIANT_SERIAL_DF = 9
+RD_FLAG_HOST_COPY = 0x4000
+RD_RNEA_KERNEL_DH_HOST = 0x209
 
 
 RD_FLAG_FAST_TRIG = 0x1000
@@ -292,9 +294,11 @@ def rnea(model, q, qd, qdd, out=None, base=None, variant=RD_VARIANT_AUTO, stream
 
 
 def rnea_host(model, q, qd, qdd, out=None, base=None, variant=RD_VARIANT_AUTO, stream=None):
-    """Inverse dynamics on host arrays (rnea_batch_host): the library copies the
-    inputs to the device, runs the kernel and copies tau back before returning.
-    Accepts CPU torch tensors or numpy arrays; pinned tensors copy fastest."""
+    """Inverse dynamics on host arrays (rnea_batch_host); returns when tau is on
+    the host. Pinned FP32 arrays (n % 4 == 0, n <= 64) are read and written in
+    place by the kernel; other arrays are staged through device buffers with
+    the copy engines (variant | RD_FLAG_HOST_COPY forces that). Accepts CPU
+    torch tensors or numpy arrays; pinned tensors move fastest."""
     import torch
 
     arrs = [q, qd, qdd]

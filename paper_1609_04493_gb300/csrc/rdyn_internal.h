@@ -62,6 +62,10 @@ int rd_rnea_dh_f32(const rd_model *m, int B, const void *q, const void *qd, cons
 int rd_rnea_dh_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
                    int kfull, int tmem, cudaStream_t s);
+// FP32 inverse dynamics reading and writing mapped pinned host arrays (device
+// addresses), n % 4 == 0, n <= 64, 16-byte aligned
+int rd_rnea_dhz_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                    void *tau, const double *base18, cudaStream_t s);
 // FP64 data in double-float arithmetic (RD_VARIANT_SERIAL_DF), n <= 64
 int rd_rnea_df_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int block, cudaStream_t s);

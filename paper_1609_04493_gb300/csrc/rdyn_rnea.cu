@@ -83,6 +83,44 @@ int enqueue_host_pipeline(rd_model *m, int B, int dtype, const void *q, const vo
     return RD_OK;
 }
 
+// Device address of a host range the GPU can read and write in place (mapped
+// pinned memory, as cudaHostAlloc gives under unified addressing), or null.
+// Both ends of the range must resolve, to consecutive device addresses.
+void *mapped_host_range(const void *p, size_t bytes)
+{
+    cudaPointerAttributes a, b;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost ||
+        static_cast<char *>(b.devicePointer) != static_cast<char *>(a.devicePointer) + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
+}
+
+// AUTO on FP32 rows the host-memory kernel takes (n % 4 == 0, n <= 64): the
+// device addresses of all four arrays when each is mapped pinned memory on a
+// 16-byte boundary.
+bool host_in_place(const rd_model *m, int B, int dtype, const void *q, const void *qd,
+                   const void *qdd, void *tau, int variant, void *dev[4])
+{
+    if (variant != RD_VARIANT_AUTO || dtype != RD_F32 || m->n % 4 != 0 || m->n > 64) return false;
+    const size_t bytes = (size_t)B * (size_t)m->n * sizeof(float);
+    const void *h[4] = {q, qd, qdd, tau};
+    for (int k = 0; k < 4; ++k) {
+        dev[k] = mapped_host_range(h[k], bytes);
+        if (!dev[k] || (reinterpret_cast<uintptr_t>(dev[k]) & 15u)) return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, const void *qd,
@@ -97,11 +135,26 @@ extern "C" int rnea_batch_host(rd_model *m, int B, int dtype, const void *q, con
     if (B == 0) return RD_OK;
     if (!q || !qd || !qdd || !tau)
         return rd_fail(RD_ERR_ARG, "rnea_batch_host: null batch pointer");
+    if (tau == q || tau == qd || tau == qdd)
+        return rd_fail(RD_ERR_ARG, "rnea_batch_host: tau aliases an input");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool copy = (variant & RD_FLAG_HOST_COPY) != 0;
+    variant &= ~RD_FLAG_HOST_COPY;
+    void *dev[4];
+    if (!copy && host_in_place(m, B, dtype, q, qd, qdd, tau, variant, dev)) {
+        // the kernel moves the rows over the host link itself (rnea_dhz.cuh)
+        double b18[18];
+        rd_convert_base(m, base, b18);
+        int rc = rd_rnea_dhz_f32(m, B, dev[0], dev[1], dev[2], dev[3], b18, s);
+        if (rc) return rc;
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_batch_host: synchronize");
+        return RD_OK;
+    }
     const size_t esz = dtype == RD_F32 ? 4 : 8;
     const size_t arr = (size_t)B * (size_t)m->n * esz;
     const size_t slot = (arr + 255) & ~(size_t)255;
     std::lock_guard<std::mutex> lk(m->io_mu);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (m->io_bytes < 4 * slot) {
         if (m->d_io) {

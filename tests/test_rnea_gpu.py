@@ -191,9 +191,10 @@ def test_rnea_host_pipeline_chunks(cuda_lib, B):
 
 
 def test_rnea_host_repeated_calls_use_current_data(cuda_lib):
-    """Repeated calls with the same pinned buffers (the device staging buffers are
-    reused): new contents in the same buffers, a new boundary state and a new
-    batch size all give the fresh result, identical to the device path."""
+    """Repeated calls with the same pinned buffers through the staged copies
+    (RD_FLAG_HOST_COPY; the device staging buffers are reused): new contents in
+    the same buffers, a new boundary state and a new batch size all give the
+    fresh result, identical to the device path."""
     torch = _torch()
     n, B = 8, 3 * 8192 + 5
     ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
@@ -207,7 +208,8 @@ def test_rnea_host_repeated_calls_use_current_data(cuda_lib):
         for bf, k in zip(bufs, ("q", "qd", "qdd")):
             bf.copy_(torch.from_numpy(st[k].astype(np.float32)))
         args = [bf[:rows] for bf in bufs]
-        tau = cuda_lib.rnea_host(model, *args, out=out[:rows], base=base).numpy().copy()
+        tau = cuda_lib.rnea_host(model, *args, out=out[:rows], base=base,
+                                 variant=cuda_lib.RD_FLAG_HOST_COPY).numpy().copy()
         dev = cuda_lib.rnea(model, *(a.cuda() for a in args), base=base).cpu().numpy()
         assert np.array_equal(tau, dev), step
         idx = np.arange(0, rows, 211)
@@ -274,3 +276,70 @@ def test_rnea_register_state_parity(cuda_lib, n, reglinks, block, dtype):
         cuda_lib.RD_TUNE_BLOCK(block)
     tau, ref = run_case(cuda_lib, n, 333, dtype, v, seed=17)
     assert oracle.rel_err(tau, ref) <= TOL[dtype]
+
+
+# ---- rnea_batch_host reading and writing mapped pinned arrays in place
+
+def _pinned_states(B, n, seed):
+    torch = _torch()
+    st = chaingen.make_states(B, n, seed=seed)
+    return [torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("q", "qd", "qdd")]
+
+
+@pytest.mark.parametrize("n,B", [(4, 1), (8, 33), (12, 1000), (32, 4097), (64, 2500)])
+def test_rnea_host_in_place(cuda_lib, n, B):
+    """Pinned FP32 arrays: the kernel reads the rows from host memory and writes
+    tau back (ragged last block included); against the oracle, and against the
+    device path within the FP32 bar (a different kernel, same recursion: both
+    carry FP32 rounding, worst case about 1e-5 of max|tau| at B = 65536)."""
+    torch = _torch()
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + 3 * n)
+    model = cuda_lib.Model(ch)
+    args = _pinned_states(B, n, seed=30 + n)
+    out = torch.full((B, n), float("nan"), dtype=torch.float32).pin_memory()
+    tau = cuda_lib.rnea_host(model, *args, out=out).numpy()
+    assert cuda_lib.rnea_last_config()[0] == cuda_lib.RD_RNEA_KERNEL_DH_HOST
+    ref = oracle.rnea(ch, *(a.numpy().astype(np.float64) for a in args))
+    assert oracle.rel_err(tau.astype(np.float64), ref) <= TOL["float32"]
+    dev = cuda_lib.rnea(model, *(a.cuda() for a in args)).cpu().numpy()
+    assert oracle.rel_err(tau.astype(np.float64), dev.astype(np.float64)) <= TOL["float32"]
+
+
+def test_rnea_host_in_place_full_batch_and_base(cuda_lib):
+    """B = 65536, n = 32 with a moving base and an end wrench: a sample against
+    the oracle; the staged-copy path on the same arrays agrees within the FP32
+    bar."""
+    torch = _torch()
+    n, B = 32, 65536
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    model = cuda_lib.Model(ch)
+    args = _pinned_states(B, n, seed=41)
+    tau = cuda_lib.rnea_host(model, *args, base=base).numpy().copy()
+    idx = np.arange(0, B, 128)
+    ref = oracle.rnea(ch, *(a.numpy()[idx].astype(np.float64) for a in args), base=base)
+    assert oracle.rel_err(tau[idx].astype(np.float64), ref) <= TOL["float32"]
+    staged = cuda_lib.rnea_host(model, *args, base=base, variant=cuda_lib.RD_FLAG_HOST_COPY).numpy()
+    assert cuda_lib.rnea_last_config()[0] != cuda_lib.RD_RNEA_KERNEL_DH_HOST
+    assert oracle.rel_err(tau.astype(np.float64), staged.astype(np.float64)) <= TOL["float32"]
+
+
+def test_rnea_host_in_place_needs_every_array_pinned_and_aligned(cuda_lib):
+    """A pageable output, or rows that start off a 16-byte boundary, take the
+    staged copies; the result is right either way."""
+    torch = _torch()
+    n, B = 8, 300
+    ch = chaingen.make_chain(n)
+    model = cuda_lib.Model(ch)
+    args = _pinned_states(B, n, seed=5)
+    ref = oracle.rnea(ch, *(a.numpy().astype(np.float64) for a in args))
+    tau = cuda_lib.rnea_host(model, *args, out=torch.empty((B, n), dtype=torch.float32)).numpy()
+    assert cuda_lib.rnea_last_config()[0] != cuda_lib.RD_RNEA_KERNEL_DH_HOST
+    assert oracle.rel_err(tau.astype(np.float64), ref) <= TOL["float32"]
+    flat = torch.empty(B * n + 1, dtype=torch.float32).pin_memory()
+    flat[1:] = args[0].reshape(-1)
+    shifted = [flat[1:].view(B, n), args[1], args[2]]
+    tau = cuda_lib.rnea_host(model, *shifted).numpy()
+    assert cuda_lib.rnea_last_config()[0] != cuda_lib.RD_RNEA_KERNEL_DH_HOST
+    assert oracle.rel_err(tau.astype(np.float64), ref) <= TOL["float32"]
