@@ -152,9 +152,11 @@ __device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, con
 // double-float pairs); qr, qdr, taur, qddr: its joint rows (VEC: n % 4 == 0 and
 // 16-byte aligned, else element loads); ws / wsz and (B, b): its workspace
 // (aba_put; Z is the type of the solve state and of the z_hat / lambda
-// recursions: D, or T). Returns 1 when an Omega_i <= 0 or a non-finite qdd
+// recursions: D, or T). PF: constants, records and workspace live in global
+// memory (fleets), and each sweep prefetches the next link's into L1 while it
+// computes the current one. Returns 1 when an Omega_i <= 0 or a non-finite qdd
 // appeared.
-template <typename T, typename D, typename Z, int TRIG, bool VEC>
+template <typename T, typename D, typename Z, int TRIG, bool VEC, bool PF = false>
 __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
                                                const T *__restrict__ qr, const T *__restrict__ qdr,
                                                const T *__restrict__ taur, T *__restrict__ qddr,
@@ -177,6 +179,7 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
         for (int j = 0; j < 4; ++j) {
             const int i = i0 + j;
             if (VEC || i < n) {
+                if (PF && i + 1 < n) prefetch_l1(sc + (i + 1) * kDhConsts);
                 DhLink<T> L;
                 load_dh(sc + i * kDhConsts, L);
                 T s, c;
@@ -214,6 +217,13 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
     D cn = D(1), sn = D(0);  // cos, sin of link i+1 in D
     // one link of the sweep, given tau_i
     auto step2 = [&](int i, T tau_i) {
+        if (PF && i > 0) {  // link i-1: records, constants, workspace
+            const D *rp = sd + (i - 1) * kAbaDh64;
+            prefetch_l1(rp);
+            prefetch_l1(rp + kAbaDh64 / 2);
+            prefetch_l1(sc + (i - 1) * kDhConsts);
+            prefetch_l1(&ws[(size_t)(i - 1) * kAbaStateScalars * B + b]);
+        }
         Wrench<T> Fh;
         Fh.f = mk3(aba_get(ws, B, b, i, 0), aba_get(ws, B, b, i, 1), aba_get(ws, B, b, i, 2));
         Fh.n = mk3(aba_get(ws, B, b, i, 3), aba_get(ws, B, b, i, 4), aba_get(ws, B, b, i, 5));
@@ -297,6 +307,12 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
     V3<Z> lv = mk3(Z(0), Z(0), Z(0)), lw = mk3(Z(0), Z(0), Z(0));
     // one link of the sweep; returns qdd_i
     auto step3 = [&](int i) -> T {
+        if (PF && i + 1 < n) {  // link i+1: records, solve state
+            const D *rp = sd + (i + 1) * kAbaDh64;
+            prefetch_l1(rp);
+            prefetch_l1(rp + kAbaDh64 / 2);
+            prefetch_l1(&wsz[(size_t)(i + 1) * kAbaSolveScalars * B + b]);
+        }
         const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
         DhRot<Z> R;
         V3<Z> bi;

@@ -26,7 +26,8 @@ namespace rdyn {
 // do not hide the global fma(double, double, double).
 namespace dfloat {
 
-struct DF {
+// 8-byte aligned, so a pair moves with one 64-bit load or store
+struct alignas(8) DF {
     float hi, lo;
     DF() = default;
     __host__ __device__ constexpr DF(float h, float l) : hi(h), lo(l) {}

@@ -10,7 +10,8 @@
 // with its inertia updates and solves in double-float arithmetic for FP32
 // data, FP64 for FP64 data) in the common-normal frames of spatial_dh.cuh,
 // reading its robot's constants from global memory since no two requests need
-// share them.
+// share them; each link prefetches the next link's constants (and, in forward
+// dynamics, records and workspace) into L1 while it computes.
 //
 // Scheduling: the host sorts requests (forward dynamics first, then by
 // decreasing n) so that the 32 requests a warp takes are alike.
@@ -44,7 +45,10 @@ struct FleetArgs {
     const int *req_robot;     // [R]
     const int *req_kind;      // [R] 0 = inverse, 1 = forward dynamics
     const long long *req_off; // [R] offset of the joint values
-    const long long *req_ws;  // [R] workspace offset in bytes (forward dynamics)
+    // forward-dynamics workspace of the 32 sorted positions [32 g, 32 g + 32):
+    // byte offsets of its T part ([link][10][lane]) and its solve part
+    // ([link][8][lane])
+    const long long *group_ws, *group_wz;
     int R;
     const T *q, *qd, *in2;    // in2: qdd (inverse) or tau (forward)
     T *out;                   // tau (inverse) or qdd (forward)
@@ -70,6 +74,7 @@ __device__ __forceinline__ void rnea_dh_instance(const T *__restrict__ sc, int n
     x.a = mk3(base.dV0[0], base.dV0[1], base.dV0[2]);
     x.al = mk3(base.dV0[3], base.dV0[4], base.dV0[5]);
     for (int i = 0; i < n; ++i) {
+        if (i + 1 < n) prefetch_l1(sc + (i + 1) * kDhConsts);
         DhXf<T> X;
         load_dh_xf(sc + i * kDhConsts, X);
         T s, c;
@@ -82,6 +87,7 @@ __device__ __forceinline__ void rnea_dh_instance(const T *__restrict__ sc, int n
     DhRot<T> Rn = dh_rot(T(1), T(0), T(1), T(0));
     V3<T> bn = mk3(T(0), T(0), T(0));
     for (int i = n - 1; i >= 0; --i) {
+        if (i > 0) prefetch_l1(sc + (i - 1) * kDhConsts);
         DhLink<T> L;
         load_dh(sc + i * kDhConsts, L);
         T s, c;
@@ -101,9 +107,11 @@ __device__ __forceinline__ void rnea_dh_instance(const T *__restrict__ sc, int n
     }
 }
 
+// The request at sorted position k.
 template <typename T>
-__device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int r)
+__device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int k)
 {
+    const int r = a.order[k];
     const int robot = a.req_robot[r];
     const int n = a.robot_n[robot];
     const long long lo = a.robot_link[robot];
@@ -140,13 +148,12 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int r)
     } else {
         using D = FleetUpdate<T>;
         static_assert(sizeof(D) == sizeof(double), "solve-state slots are 8 bytes");
-        unsigned char *w = a.ws + a.req_ws[r];
-        T *wt = reinterpret_cast<T *>(w);
-        D *wz = reinterpret_cast<D *>(
-            w + (((size_t)n * kAbaStateScalars * sizeof(T) + 15) & ~(size_t)15));
-        const int bad = aba_dh_instance<T, D, D, kTrigPoly, false>(
+        const int g = k >> 5;
+        T *wt = reinterpret_cast<T *>(a.ws + a.group_ws[g]);
+        D *wz = reinterpret_cast<D *>(a.ws + a.group_wz[g]);
+        const int bad = aba_dh_instance<T, D, D, kTrigPoly, false, true>(
             sc, a.records + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off, a.out + off,
-            wt, wz, 1, 0, bp);
+            wt, wz, 32, k & 31, bp);
         if (a.status) a.status[r] = bad ? 1 : 0;
     }
 }
@@ -162,7 +169,7 @@ __global__ void fleet_persistent_kernel(FleetArgs<T> a)
         start = __shfl_sync(0xffffffffu, start, 0);
         if (start >= a.R) break;
         const int k = start + lane;
-        if (k < a.R) fleet_request(a, a.order[k]);
+        if (k < a.R) fleet_request(a, k);
     }
 }
 
@@ -171,7 +178,7 @@ template <typename T>
 __global__ void fleet_range_kernel(FleetArgs<T> a, int begin, int end)
 {
     const int k = begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < end) fleet_request(a, a.order[k]);
+    if (k < end) fleet_request(a, k);
 }
 
 }  // namespace rdyn

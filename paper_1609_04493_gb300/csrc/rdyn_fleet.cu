@@ -35,7 +35,8 @@ struct rd_plan {
     std::vector<long long> off;               // user order
     std::vector<std::pair<int, int>> groups;  // sorted positions [begin, end) of equal (kind, n)
     int *order = nullptr, *req_robot = nullptr, *req_kind = nullptr, *counter = nullptr;
-    long long *req_off = nullptr, *req_ws = nullptr;
+    long long *req_off = nullptr;
+    long long *group_ws = nullptr, *group_wz = nullptr;  // per 32 sorted positions
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     int sms = 0;
@@ -150,7 +151,8 @@ extern "C" void rd_plan_destroy(rd_plan *p)
     cudaFree(p->req_kind);
     cudaFree(p->counter);
     cudaFree(p->req_off);
-    cudaFree(p->req_ws);
+    cudaFree(p->group_ws);
+    cudaFree(p->group_wz);
     cudaFree(p->ws);
     for (int k = 0; k < rd_plan::kSide; ++k) {
         if (p->side[k]) cudaStreamDestroy(p->side[k]);
@@ -170,7 +172,7 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
     if (R < 1) return rd_fail(RD_ERR_RANGE, "rd_plan_create: R = %d", R);
     if (dtype != RD_F32 && dtype != RD_F64) return rd_fail(RD_ERR_DTYPE, "rd_plan_create: dtype %d", dtype);
     const size_t esz = dtype == RD_F32 ? 4 : 8;
-    std::vector<long long> off(R), wsoff(R, 0);
+    std::vector<long long> off(R);
     long long tot = 0;
     for (int r = 0; r < R; ++r) {
         if (robot[r] < 0 || robot[r] >= f->nrobots)
@@ -187,13 +189,21 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
         if (kind[a] != kind[b]) return kind[a] > kind[b];
         return f->n[robot[a]] > f->n[robot[b]];
     });
+    // forward-dynamics workspace per group of 32 sorted positions, laid out
+    // [link][component][lane] so that a warp's accesses coalesce; sized by the
+    // group's longest forward-dynamics chain
+    const int groups32 = (R + 31) / 32;
+    std::vector<long long> gws(groups32, 0), gwz(groups32, 0);
     size_t ws = 0;
-    for (int k = 0; k < R; ++k) {
-        const int r = order[k];
-        if (kind[r] != RD_REQ_FD) continue;
-        const size_t nl = (size_t)f->n[robot[r]];
-        wsoff[r] = (long long)ws;
-        ws += ((nl * 10 * esz + 15) & ~(size_t)15) + ((nl * 8 * 8 + 15) & ~(size_t)15);
+    for (int g = 0; g < groups32; ++g) {
+        size_t nmax = 0;
+        for (int k = 32 * g; k < R && k < 32 * g + 32; ++k)
+            if (kind[order[k]] == RD_REQ_FD) nmax = std::max(nmax, (size_t)f->n[robot[order[k]]]);
+        if (!nmax) continue;
+        gws[g] = (long long)ws;
+        ws += (nmax * 10 * 32 * esz + 255) & ~(size_t)255;
+        gwz[g] = (long long)ws;
+        ws += (nmax * 8 * 32 * 8 + 255) & ~(size_t)255;
     }
     rd_plan *p = new (std::nothrow) rd_plan();
     if (!p) return rd_fail(RD_ERR_ALLOC, "rd_plan_create: host allocation failed");
@@ -214,7 +224,8 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
     if (e == cudaSuccess) e = upload(&p->req_robot, robot, (size_t)R);
     if (e == cudaSuccess) e = upload(&p->req_kind, kind, (size_t)R);
     if (e == cudaSuccess) e = upload(&p->req_off, off.data(), off.size());
-    if (e == cudaSuccess) e = upload(&p->req_ws, wsoff.data(), wsoff.size());
+    if (e == cudaSuccess) e = upload(&p->group_ws, gws.data(), gws.size());
+    if (e == cudaSuccess) e = upload(&p->group_wz, gwz.data(), gwz.size());
     if (e == cudaSuccess) e = cudaMalloc(&p->counter, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&p->ws, std::max<size_t>(ws, 16));
     p->ws_bytes = ws;
@@ -267,7 +278,8 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
     a.req_robot = p->req_robot;
     a.req_kind = p->req_kind;
     a.req_off = p->req_off;
-    a.req_ws = p->req_ws;
+    a.group_ws = p->group_ws;
+    a.group_wz = p->group_wz;
     a.R = p->R;
     a.q = static_cast<const T *>(q);
     a.qd = static_cast<const T *>(qd);
