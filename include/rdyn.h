@@ -61,12 +61,13 @@ enum rd_status {
 /* aba_batch flag: run the joint-frame kernel even where the common-normal one
  * applies (n % 4 == 0, n <= 64, 16-byte aligned rows), for comparisons. */
 #define RD_ABA_JOINT_FRAMES 0x2
-/* aba_batch flag, RD_F32 only. By default, where the common-normal kernel
- * applies, the articulated-inertia update, the Omega solves and the z_hat /
- * lambda recursions of FP32 data run in double-float arithmetic (a value is the
- * unevaluated sum of two FP32 numbers, about 48 significand bits; Dekker 1971)
- * on the FP32 pipe. This flag runs them in hardware FP64 instead. Ignored for
- * RD_F64. */
+/* aba_batch flag, RD_F32 only. By default the articulated-inertia update, the
+ * Omega solves and the z_hat / lambda recursions of FP32 data run in
+ * double-float arithmetic (a value is the unevaluated sum of two FP32 numbers,
+ * about 48 significand bits; Dekker 1971) on the FP32 pipe, in common-normal
+ * frames (constants as a kernel parameter for n % 4 == 0, n <= 64 and aligned
+ * rows; in global memory otherwise). This flag runs them in hardware FP64
+ * instead. Ignored for RD_F64. */
 #define RD_ABA_FP64_UPDATE 0x4
 
 /* Per-instance status word of aba_batch (0 = fine). */
@@ -292,9 +293,8 @@ int rnea_vjp_noalloc(const rd_model *model, int B, int dtype, const void *q, con
  * the articulated-body inertias (Eq. abi), and the backward / forward linear
  * recursions of Eq. recursive-fd (the scans of Sec. III-D; Algorithm 3 without
  * its CPU stage). Arithmetic in dtype, except the articulated-inertia update
- * and the divisions by Omega_i = S_i^T J_hat_i S_i: FP64 for RD_F64 data and in
- * the joint-frame kernel; double-float (about 48 bits, see RD_ABA_FP64_UPDATE)
- * for RD_F32 data in the common-normal kernel.
+ * and the divisions by Omega_i = S_i^T J_hat_i S_i: FP64 for RD_F64 data (and
+ * with RD_ABA_FP64_UPDATE); double-float (about 48 bits) for RD_F32 data.
  *
  *   q, qd, tau  device, [B, n] row-major inputs; qdd device [B, n] output.
  *   base        as in rnea_batch.

@@ -374,4 +374,24 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, D, NMAX> pc, int n, int B,
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }
 
+// Forward dynamics of FP32 data with the constants and the double-float records
+// in global memory, for what the parameter space does not take: chains longer
+// than 64 links, lengths not a multiple of 4, unaligned rows (VEC = false). The
+// sweeps prefetch each next link's constants, records and workspace into L1.
+template <typename Z, int BLOCK, bool VEC>
+__global__ void __launch_bounds__(BLOCK, 384 / BLOCK)
+aba_dhg_kernel(const float *__restrict__ sc, const DF *__restrict__ sd, int n, int B,
+               const float *__restrict__ q, const float *__restrict__ qd,
+               const float *__restrict__ tau, float *__restrict__ qdd_out,
+               int *__restrict__ status, float *__restrict__ ws, Z *__restrict__ wsz,
+               BaseParams<float> base)
+{
+    const int b = blockIdx.x * BLOCK + threadIdx.x;
+    if (b >= B) return;
+    const size_t row = (size_t)b * (size_t)n;
+    const int bad = aba_dh_instance<float, DF, Z, kTrigPoly, VEC, true>(
+        sc, sd, n, q + row, qd + row, tau + row, qdd_out + row, ws, wsz, B, b, base);
+    if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
+}
+
 }  // namespace rdyn

@@ -104,6 +104,32 @@ int launch_aba_dh(const rd_model *m, int B, const void *q, const void *qd, const
     return launch_aba_dh_k<T, D, Z, 64, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
 
+template <typename Z, bool VEC>
+int launch_aba_dhg(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                   void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
+{
+    constexpr int BLOCK = 64;
+    const int n = m->n;
+    double bb[18];
+    rd_convert_base_dh(m, base18, bb);
+    BaseParams<float> bp;
+    for (int k = 0; k < 6; ++k) {
+        bp.V0[k] = (float)bb[k];
+        bp.dV0[k] = (float)bb[6 + k];
+        bp.Fn[k] = (float)bb[12 + k];
+    }
+    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(float);
+    Z *wsz = reinterpret_cast<Z *>(static_cast<char *>(ws) + ((a + 255) & ~(size_t)255));
+    const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
+    aba_dhg_kernel<Z, BLOCK, VEC><<<grid, BLOCK, 0, stream>>>(
+        m->d_dh32, reinterpret_cast<const DF *>(m->d_abadf), n, B, static_cast<const float *>(q),
+        static_cast<const float *>(qd), static_cast<const float *>(tau), static_cast<float *>(qdd),
+        status, static_cast<float *>(ws), wsz, bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "aba double-float kernel launch");
+    return RD_OK;
+}
+
 template <typename T>
 int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                  void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
@@ -130,6 +156,14 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
         return launch_aba_dh<T, double, double>(m, B, q, qd, tau, qdd, status, ws, base18, s);
     }
     if constexpr (sizeof(T) == 4) {
+        if (!(flags & (RD_ABA_JOINT_FRAMES | RD_ABA_FP64_UPDATE))) {
+            // common-normal frames, constants and double-float records in global memory
+            if (fp32_scans)
+                return vec ? launch_aba_dhg<float, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+                           : launch_aba_dhg<float, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+            return vec ? launch_aba_dhg<DF, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+                       : launch_aba_dhg<DF, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+        }
         if (fp32_scans)
             return vec ? launch_aba_k<T, T, 64, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
                        : launch_aba_k<T, T, 64, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);

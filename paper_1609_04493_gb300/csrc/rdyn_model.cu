@@ -394,6 +394,17 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
         e = cudaMemcpy(mdl->d_dh64, dh64.data(), dh64.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(mdl->d_dh32, dh32.data(), dh32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    // double-float pairs of the forward-dynamics records: hi = nearest float,
+    // lo = nearest float of the remainder
+    std::vector<float> abadf(2 * mdl->host_aba64.size());
+    for (size_t k = 0; k < mdl->host_aba64.size(); ++k) {
+        const double v = mdl->host_aba64[k];
+        abadf[2 * k] = (float)v;
+        abadf[2 * k + 1] = (float)(v - (double)(float)v);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&mdl->d_abadf, abadf.size() * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(mdl->d_abadf, abadf.data(), abadf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         rd_model_destroy(mdl);
         return e == cudaErrorMemoryAllocation ? rd_fail(RD_ERR_ALLOC, "rd_model_create: %s",
@@ -414,6 +425,7 @@ extern "C" void rd_model_destroy(rd_model *m)
     if (m->d_c64) cudaFree(m->d_c64);
     if (m->d_dh32) cudaFree(m->d_dh32);
     if (m->d_dh64) cudaFree(m->d_dh64);
+    if (m->d_abadf) cudaFree(m->d_abadf);
     if (m->d_io) cudaFree(m->d_io);
     if (m->io_in) cudaStreamDestroy(m->io_in);
     if (m->io_out) cudaStreamDestroy(m->io_out);

@@ -246,3 +246,67 @@ def test_aba_double_float_flags_a_singular_joint(cuda_lib):
     status = torch.full((6,), -7, dtype=torch.int32, device="cuda")
     cuda_lib.aba(model, x, x, x + 1.0, status=status)
     assert torch.all(status == 1)
+
+
+# ---- FP32 data beyond the parameter-constant kernel: constants and double-float
+# records in global memory (n > 64, n % 4 != 0, unaligned rows)
+
+@pytest.mark.parametrize("n", [3, 5, 65, 100])
+def test_aba_global_constant_kernel_matches_oracle(cuda_lib, n):
+    qdd, ch, h, _ = run(cuda_lib, n, 400, "float32", seed=59)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    assert oracle.rel_err(qdd, ref) <= TOL["float32"], f"n={n}"
+
+
+def test_aba_long_chain_n128(cuda_lib):
+    """n = 128 in FP32 data, on a bar scaled with the chain length,
+    1e-3 * n / 64: the error grows along the chain with the FP32 bias sweeps
+    (tau_hat = tau - tau_bias cancels against bias torques far above tau), which
+    the precision of the inertia update does not change; the FP64-update path
+    (joint frames beyond 64 links) is printed beside it."""
+    n = 128
+    a, ch, h, _ = run(cuda_lib, n, 400, "float32", seed=59)
+    b, _, _, _ = run(cuda_lib, n, 400, "float32", seed=59, flags=cuda_lib.RD_ABA_FP64_UPDATE)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    ea, eb = oracle.rel_err(a, ref), oracle.rel_err(b, ref)
+    print(f"n = 128 FP32: double-float update {ea:.3e}, FP64 update (joint frames) {eb:.3e}")
+    assert ea <= TOL["float32"] * n / 64
+    assert eb <= TOL["float32"] * n / 64
+
+
+def test_aba_global_constant_kernel_unaligned_rows_and_base(cuda_lib):
+    """Rows off a 16-byte boundary (element loads), with base motion and an end
+    wrench."""
+    import torch
+
+    n, B = 8, 300
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    ch = chaingen.make_chain(n, seed=77)
+    st = chaingen.make_states(B, n, seed=78, kinds=("q", "qd", "tau"))
+    model = cuda_lib.Model(ch)
+    bufs = []
+    for k in ("q", "qd", "tau"):
+        flat = torch.zeros(B * n + 1, dtype=torch.float32, device="cuda")
+        flat[1:] = torch.from_numpy(st[k].astype(np.float32).ravel()).cuda()
+        bufs.append(flat[1:].view(B, n))
+    out = torch.zeros(B * n + 1, dtype=torch.float32, device="cuda")[1:].view(B, n)
+    qdd = cuda_lib.aba(model, *bufs, base=base, out=out).cpu().double().numpy()
+    h = {k: st[k].astype(np.float32).astype(np.float64) for k in st}
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=base)
+    assert oracle.rel_err(qdd, ref) <= TOL["float32"]
+
+
+def test_aba_global_constant_kernel_full_batch_n100(cuda_lib):
+    """B = 16384, n = 100: every 64th instance against the oracle, and the
+    round-trip residual on the scale of test_aba_full_batch_sampled."""
+    n, B = 100, 16384
+    qdd, ch, h, _ = run(cuda_lib, n, B, "float32", seed=1609)
+    idx = np.arange(0, B, 64)
+    ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
+    assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
+    back = oracle.rnea(ch, h["q"][idx], h["qd"][idx], qdd[idx])
+    bias = oracle.rnea(ch, h["q"][idx], h["qd"][idx], np.zeros_like(qdd[idx]))
+    scale = np.maximum(np.max(np.abs(h["tau"][idx]), axis=1), np.max(np.abs(bias), axis=1))
+    err = np.max(np.abs(back - h["tau"][idx]), axis=1) / scale
+    assert err.max() <= 1e-4 * n / 16, err.max()
