@@ -33,6 +33,13 @@
 
 namespace rdyn {
 
+// Hint: bring the 128-byte line holding p into L1 ahead of its use. Only for
+// addresses in global memory (not kernel parameters).
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.L1 [%0];" ::"l"(p));
+}
+
 // FP64 record of a link: the 16 common-normal constants (spatial_dh.cuh), then
 // m c (3), the rotational inertia about the frame origin C_o = I_c + m (|c|^2 -
 // c c^T) (xx, yy, zz, xy, xz, yz), and cos^2 alpha, sin^2 alpha, cos alpha sin

@@ -13,13 +13,6 @@
 
 namespace rdyn {
 
-// Hint: bring the 128-byte line holding p into L1 ahead of its use. Only for
-// addresses in global memory (not kernel parameters).
-__device__ __forceinline__ void prefetch_l1(const void *p)
-{
-    asm volatile("prefetch.L1 [%0];" ::"l"(p));
-}
-
 template <typename T>
 struct V3 {
     T x, y, z;
