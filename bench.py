@@ -365,32 +365,33 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
                 rd.aba(model, *x, workspace=ws, out=o, flags=flags)
             return time_calls(torch, call, steps, 3, dist, sampler)
 
-        t = timed(0)
         t64 = timed(rd.RD_ABA_FP64_UPDATE)
-        t_exec = B * n * FD_DF_EXEC_FP32_INST_PER_LINK / inst_rate
-        t_floor = B * n * FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12)
+        tdf = timed(0)
         t_exec64 = B * n * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
                             + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
-        out[f"n{n}_B{B}"] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
-                             "steps": steps, "roofline_ms": t_exec * 1e3,
-                             "roofline_frac": t_exec / (t / steps),
+        t_floor = B * n * FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12)
+        t_exec = B * n * FD_DF_EXEC_FP32_INST_PER_LINK / inst_rate
+        out[f"n{n}_B{B}"] = {"value": B * steps / t64, "unit": UNIT,
+                             "ms_per_step": t64 / steps * 1e3, "steps": steps,
+                             "roofline_ms": t_exec64 * 1e3,
+                             "roofline_frac": t_exec64 / (t64 / steps),
                              "fp64_pipe_floor_ms": t_floor * 1e3,
-                             "fp64_update": {"value": B * steps / t64,
-                                             "ms_per_step": t64 / steps * 1e3,
-                                             "roofline_ms": t_exec64 * 1e3,
-                                             "roofline_frac": t_exec64 / (t64 / steps)}}
+                             "double_float": {"value": B * steps / tdf,
+                                              "ms_per_step": tdf / steps * 1e3,
+                                              "roofline_ms": t_exec * 1e3,
+                                              "roofline_frac": t_exec / (tdf / steps)}}
     out["algorithmic_flop_per_link"] = {"fp32": FD_FLOP32_PER_LINK,
                                          "extended_precision": FD_FLOP64_PER_LINK}
-    out["metric"] = ("forward dynamics (articulated-body, FP32 data; inertia updates and solves "
-                     "in double-float arithmetic, and beside it in FP64) evals/s")
-    out["roofline"] = (f"double-float default: FP32-pipe issue time of the kernel's "
-                       f"{FD_DF_EXEC_FP32_INST_PER_LINK} FP32 instructions per link at "
-                       f"{SM_COUNT} x {FP32_LANES_PER_SM} lanes x 2.07 GHz, divided by the "
-                       f"measured time; fp64_pipe_floor_ms: the time the FP64 pipe needs for the "
-                       f"update's {FD_EXEC_FLOP64_PER_LINK} FP64 flop per link at the nominal "
-                       f"FP64 peak, which the FP64 kernel cannot beat; fp64_update: combined FP32 "
-                       f"+ FP64 time of its {FD_EXEC_FLOP32_PER_LINK} FP32 and "
-                       f"{FD_EXEC_FLOP64_PER_LINK} FP64 flop per link")
+    out["metric"] = ("forward dynamics (articulated-body, FP32 data, FP64 inertia updates and "
+                     "solves as the workload specifies; beside it the library's default, the "
+                     "same in double-float arithmetic) evals/s")
+    out["roofline"] = (f"FP64 updates: combined FP32 + FP64 time of the kernel's "
+                       f"{FD_EXEC_FLOP32_PER_LINK} FP32 and {FD_EXEC_FLOP64_PER_LINK} FP64 flop "
+                       f"per link at the derived FP32 and nominal FP64 peaks, divided by the "
+                       f"measured time; fp64_pipe_floor_ms: the FP64 part alone; double_float: "
+                       f"FP32-pipe issue time of its {FD_DF_EXEC_FP32_INST_PER_LINK} FP32 "
+                       f"instructions per link at {SM_COUNT} x {FP32_LANES_PER_SM} lanes x "
+                       f"2.07 GHz")
     return out
 
 
@@ -408,11 +409,14 @@ def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
     x = [torch.from_numpy(a.astype(np.float32)).to(dev)
          for a in (rng.uniform(-np.pi, np.pi, J), rng.normal(0, 1, J), in2)]
     o = torch.empty_like(x[0])
-    (sched, tune), _ = autotune.tune_fleet(plan, *x, out=o)
+    f64 = rd.RD_FLEET_FP64_UPDATE
+    (sched, tune), _ = autotune.tune_fleet(plan, *x, out=o, flags=f64)
+    (sched_df, tune_df), _ = autotune.tune_fleet(plan, *x, out=o)
     steps = max(3, min(K, 20))
     res = {}
-    for name, (sc, tu) in (("persistent_tuned", (sched, tune)),
-                           ("per_group_launches", (rd.RD_SCHED_PER_GROUP, 0))):
+    for name, (sc, tu) in (("persistent_tuned", (sched | f64, tune)),
+                           ("per_group_launches", (rd.RD_SCHED_PER_GROUP | f64, 0)),
+                           ("double_float_persistent_tuned", (sched_df, tune_df))):
         t = time_calls(torch, lambda k: rd.fleet_batch(plan, *x, out=o, schedule=sc, tune=tu),
                        steps, 3, dist, sampler)
         res[name] = {"value": count * steps / t, "unit": "requests/s",
@@ -420,21 +424,27 @@ def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
                      "schedule": sc, "tune": tu}
     n_fd = int(np.sum(np.where(kinds == 1, plan.lengths, 0)))
     n_id = J - n_fd
-    t_alg = (n_id * max(ALGO_FLOP_PER_LINK / (fp32_peak_tflops() * 1e12),
-                        UNEVEN_ID_BYTES_PER_LINK / (measured_peaks().get("hbm_gbs", 6800.0) * 1e9))
-             + n_fd * FD_DF_EXEC_FP32_INST_PER_LINK / (SM_COUNT * FP32_LANES_PER_SM * 2.070e9))
+    t_id = n_id * max(ALGO_FLOP_PER_LINK / (fp32_peak_tflops() * 1e12),
+                      UNEVEN_ID_BYTES_PER_LINK / (measured_peaks().get("hbm_gbs", 6800.0) * 1e9))
+    t_alg = t_id + n_fd * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
+                           + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
+    t_alg_df = t_id + n_fd * FD_DF_EXEC_FP32_INST_PER_LINK / (SM_COUNT * FP32_LANES_PER_SM * 2.070e9)
     for name in ("persistent_tuned", "per_group_launches"):
         res[name]["roofline_frac"] = t_alg / (res[name]["ms_per_step"] * 1e-3)
+    res["double_float_persistent_tuned"]["roofline_frac"] = t_alg_df / (
+        res["double_float_persistent_tuned"]["ms_per_step"] * 1e-3)
     res["roofline_ms"] = t_alg * 1e3
     res["roofline"] = (f"inverse dynamics links at the larger of {ALGO_FLOP_PER_LINK} flop / FP32 "
                        f"peak and {UNEVEN_ID_BYTES_PER_LINK} B (joint values, torque, streamed "
                        f"constants) / measured HBM bandwidth, plus forward dynamics links at the "
-                       f"FP32-pipe issue time of the double-float kernel's "
-                       f"{FD_DF_EXEC_FP32_INST_PER_LINK} instructions per link; divided by the "
-                       f"measured time")
+                       f"combined FP32 + FP64 time of {FD_EXEC_FLOP32_PER_LINK} FP32 and "
+                       f"{FD_EXEC_FLOP64_PER_LINK} FP64 flop per link (double-float line: the "
+                       f"FP32-pipe issue time of {FD_DF_EXEC_FP32_INST_PER_LINK} instructions "
+                       f"per link); divided by the measured time")
     res["workload"] = (f"{count} requests, own robot each, n uniform in 6..100 "
                        f"({J} joints), {int(kinds.sum())} forward / {count - int(kinds.sum())} "
-                       f"inverse dynamics, FP32 (double-float inertia updates and solves)")
+                       f"inverse dynamics, FP32 with FP64 inertia updates and solves (the "
+                       f"double-float line: the library's default)")
     res["launches_per_group_schedule"] = plan.groups
     return res
 

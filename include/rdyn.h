@@ -340,6 +340,10 @@ enum rd_schedule {
     RD_SCHED_PER_GROUP = 1   /* one launch per run of equal (kind, n), spread over 8
                                 side streams forked from and joined into the call's stream */
 };
+/* OR-able with the schedule: forward-dynamics requests of an RD_F32 plan run their
+ * inertia updates and solves in FP64 instead of the default double-float
+ * arithmetic (as RD_ABA_FP64_UPDATE for aba_batch). */
+#define RD_FLEET_FP64_UPDATE 0x10
 /* Tuning word for RD_SCHED_PERSISTENT: threads per CTA = 2^t, CTAs per SM = c
  * (0 = library default: 128 threads, 4 CTAs per SM). */
 #define RD_FLEET_TUNE(log2_threads, ctas_per_sm) (((log2_threads) << 8) | (ctas_per_sm))
@@ -359,8 +363,9 @@ void rd_fleet_destroy(rd_fleet *fleet);
  * rd_plan_create -- a fixed set of R requests on a fleet, for data type dtype.
  *   robot    host int[R]: robot of each request.
  *   kind     host int[R]: RD_REQ_ID (tau from q, qd, qdd) or RD_REQ_FD (qdd from
- *            q, qd, tau; articulated-body algorithm with FP64 inertia updates and
- *            solves, as aba_batch).
+ *            q, qd, tau; articulated-body algorithm as aba_batch: inertia updates
+ *            and solves in double-float arithmetic for RD_F32 plans, or FP64 with
+ *            RD_FLEET_FP64_UPDATE, and FP64 for RD_F64 plans).
  * Joint data of a call is ragged: request r uses elements [off_r, off_r + n_r)
  * of every array, off_r the running sum of n over earlier requests
  * (rd_plan_offsets). The plan sorts requests (forward dynamics first, then by
@@ -386,7 +391,7 @@ int rd_plan_groups(const rd_plan *plan);
  *            frame n), or NULL for rest under gravity along -z.
  *   status   device int[R] or NULL: RD_WARN_SINGULAR for a forward-dynamics
  *            request that met Omega_i <= 0 or a non-finite qdd.
- *   schedule rd_schedule; tune: RD_FLEET_TUNE(...) or 0.
+ *   schedule rd_schedule, optionally | RD_FLEET_FP64_UPDATE; tune: RD_FLEET_TUNE(...) or 0.
  * Concurrent calls on one plan race on its counter and workspace.
  */
 int fleet_batch(const rd_plan *plan, const void *q, const void *qd, const void *in2, void *out,

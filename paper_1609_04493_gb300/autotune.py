@@ -130,14 +130,18 @@ def fleet_candidates():
     return c
 
 
-def tune_fleet(plan, q, qd, in2, out=None, reps=3, use_cache=True):
-    """Fastest (schedule, tune word) for this plan's request mix; returns
-    ((schedule, tune), {(schedule, tune): ms})."""
+def tune_fleet(plan, q, qd, in2, out=None, reps=3, use_cache=True, flags=0):
+    """Fastest (schedule, tune word) for this plan's request mix, every candidate
+    run with ``flags`` (e.g. RD_FLEET_FP64_UPDATE) OR-ed into its schedule;
+    returns ((schedule, tune), {(schedule, tune): ms}) without the flags."""
+    import zlib
+
     import numpy as np
     import torch
 
     hist = np.bincount(plan.lengths * 2 + plan.kinds, minlength=2 * 130)
-    sig = f"R={plan.R}|J={plan.total_joints}|h={hash(hist.tobytes()) & 0xffffffff:x}|{plan.dtype}"
+    sig = (f"R={plan.R}|J={plan.total_joints}|h={zlib.crc32(hist.tobytes()):08x}|{plan.dtype}"
+           f"|f={int(flags):x}")
     key = f"fleet|{_gpu_key(torch, q.device)}|{sig}"
     if use_cache:
         hit = _load_cache().get(key)
@@ -147,7 +151,8 @@ def tune_fleet(plan, q, qd, in2, out=None, reps=3, use_cache=True):
     times = {}
     for sched, tune in fleet_candidates():
         times[(sched, tune)] = _time(
-            torch, lambda: b.fleet_batch(plan, q, qd, in2, out=out, schedule=sched, tune=tune), reps)
+            torch, lambda: b.fleet_batch(plan, q, qd, in2, out=out, schedule=sched | flags,
+                                         tune=tune), reps)
     best = min(times, key=times.get)
     _store(key, {"schedule": best[0], "tune": best[1],
                  "times": {f"{k[0]}:{k[1]}": t for k, t in times.items()}})

@@ -446,6 +446,7 @@ RD_REQ_ID = 0
 RD_REQ_FD = 1
 RD_SCHED_PERSISTENT = 0
 RD_SCHED_PER_GROUP = 1
+RD_FLEET_FP64_UPDATE = 0x10
 
 
 def RD_FLEET_TUNE(log2_threads, ctas_per_sm):

@@ -8,7 +8,8 @@
 // request with the per-instance bodies of the single-chain kernels (the
 // re-derive-in-the-backward-sweep RNEA, and the articulated-body algorithm
 // with its inertia updates and solves in double-float arithmetic for FP32
-// data, FP64 for FP64 data) in the common-normal frames of spatial_dh.cuh,
+// data unless FP64 is asked for, FP64 for FP64 data) in the common-normal
+// frames of spatial_dh.cuh,
 // reading its robot's constants from global memory since no two requests need
 // share them; each link prefetches the next link's constants (and, in forward
 // dynamics, records and workspace) into L1 while it computes.
@@ -22,21 +23,17 @@
 //   per-group:  one ordinary launch per run of equal (kind, n) in the sorted
 //               order -- the "one launch per request size" comparison.
 #pragma once
-#include <type_traits>
-
 #include "aba_dh.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
 
-// scalar of the forward-dynamics inertia updates and solves for data type T
-template <typename T>
-using FleetUpdate = typename std::conditional<sizeof(T) == 4, DF, double>::type;
-
-template <typename T>
+// T: data type; D: scalar of the forward-dynamics inertia updates and solves
+// (double-float for FP32 data by default, else double)
+template <typename T, typename D>
 struct FleetArgs {
     const T *consts;          // [total links][16] common-normal constants
-    const FleetUpdate<T> *records;  // [total links][32] forward-dynamics records
+    const D *records;         // [total links][32] forward-dynamics records
     const int *robot_n;       // [robots]
     const int *robot_link;    // [robots] first constant row
     const T *robot_gb;        // [robots][12] base frame D_{-1} in frame 0: R (9), p (3)
@@ -108,8 +105,8 @@ __device__ __forceinline__ void rnea_dh_instance(const T *__restrict__ sc, int n
 }
 
 // The request at sorted position k.
-template <typename T>
-__device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int k)
+template <typename T, typename D>
+__device__ __forceinline__ void fleet_request(const FleetArgs<T, D> &a, int k)
 {
     const int r = a.order[k];
     const int robot = a.req_robot[r];
@@ -146,7 +143,6 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int k)
     if (a.req_kind[r] == 0) {
         rnea_dh_instance<T, kTrigPoly>(sc, n, a.q + off, a.qd + off, a.in2 + off, a.out + off, bp);
     } else {
-        using D = FleetUpdate<T>;
         static_assert(sizeof(D) == sizeof(double), "solve-state slots are 8 bytes");
         const int g = k >> 5;
         T *wt = reinterpret_cast<T *>(a.ws + a.group_ws[g]);
@@ -159,8 +155,8 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T> &a, int k)
 }
 
 // Persistent: warps take 32 sorted requests at a time until none are left.
-template <typename T>
-__global__ void fleet_persistent_kernel(FleetArgs<T> a)
+template <typename T, typename D>
+__global__ void fleet_persistent_kernel(FleetArgs<T, D> a)
 {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -174,8 +170,8 @@ __global__ void fleet_persistent_kernel(FleetArgs<T> a)
 }
 
 // One ordinary launch over sorted positions [begin, end).
-template <typename T>
-__global__ void fleet_range_kernel(FleetArgs<T> a, int begin, int end)
+template <typename T, typename D>
+__global__ void fleet_range_kernel(FleetArgs<T, D> a, int begin, int end)
 {
     const int k = begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (k < end) fleet_request(a, k);

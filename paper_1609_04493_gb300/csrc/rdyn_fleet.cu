@@ -8,6 +8,7 @@
 #include <atomic>
 #include <new>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "fleet.cuh"
@@ -255,23 +256,23 @@ extern "C" int rd_plan_groups(const rd_plan *p) { return p ? (int)p->groups.size
 
 namespace {
 
-template <typename T>
+template <typename T, typename D>
 int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, void *out,
               const double *b18, int *status, int schedule, int tune, cudaStream_t s)
 {
     const rd_fleet *f = p->fleet;
-    rdyn::FleetArgs<T> a;
+    rdyn::FleetArgs<T, D> a;
     if constexpr (sizeof(T) == 4) {
         a.consts = f->c32;
         a.robot_tn = f->tn32;
         a.robot_gb = f->gb32;
-        a.records = f->abadf;
     } else {
         a.consts = f->c64;
         a.robot_tn = f->tn64;
         a.robot_gb = f->gb64;
-        a.records = f->aba64;
     }
+    if constexpr (std::is_same<D, double>::value) a.records = f->aba64;
+    else a.records = f->abadf;
     a.robot_n = f->robot_n;
     a.robot_link = f->robot_link;
     a.order = p->order;
@@ -301,7 +302,7 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
             return rd_fail(RD_ERR_ARG, "fleet_batch: %d threads per block", threads);
         e = cudaMemsetAsync(p->counter, 0, sizeof(int), s);
         if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch: counter reset");
-        rdyn::fleet_persistent_kernel<T><<<p->sms * per_sm, threads, 0, s>>>(a);
+        rdyn::fleet_persistent_kernel<T, D><<<p->sms * per_sm, threads, 0, s>>>(a);
     } else if (schedule == RD_SCHED_PER_GROUP) {
         // one launch per group, spread over side streams that fork from and
         // join back into the caller's stream (so groups can run concurrently)
@@ -312,7 +313,7 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
         int k = 0;
         for (const auto &g : p->groups) {
             const int len = g.second - g.first;
-            rdyn::fleet_range_kernel<T><<<(len + 127) / 128, 128, 0, p->side[k]>>>(a, g.first, g.second);
+            rdyn::fleet_range_kernel<T, D><<<(len + 127) / 128, 128, 0, p->side[k]>>>(a, g.first, g.second);
             k = (k + 1) % rd_plan::kSide;
         }
         for (int j = 0; j < rd_plan::kSide && e == cudaSuccess; ++j) {
@@ -342,6 +343,12 @@ extern "C" int fleet_batch(const rd_plan *p, const void *q, const void *qd, cons
     static const double dflt[18] = {0, 0, 0, 0, 0, 0, 0, 0, 9.81, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const double *b18 = base ? base : dflt;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->dtype == RD_F32) return run_fleet<float>(p, q, qd, in2, out, b18, status, schedule, tune, s);
-    return run_fleet<double>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+    const bool fp64_update = (schedule & RD_FLEET_FP64_UPDATE) != 0;
+    schedule &= ~RD_FLEET_FP64_UPDATE;
+    if (p->dtype == RD_F32) {
+        if (fp64_update)
+            return run_fleet<float, double>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+        return run_fleet<float, rdyn::DF>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+    }
+    return run_fleet<double, double>(p, q, qd, in2, out, b18, status, schedule, tune, s);
 }

@@ -119,3 +119,23 @@ def test_autotuner_picks_a_working_configuration(cuda_lib, tmp_path, monkeypatch
     tau = cuda_lib.rnea(model, *x, variant=v).cpu().numpy()
     ref = oracle.rnea(ch, *(a.cpu().double().numpy() for a in x))
     assert oracle.rel_err(tau, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_fleet_fp64_update_flag(cuda_lib, schedule):
+    """FP32 plan with RD_FLEET_FP64_UPDATE: the forward-dynamics requests run
+    their inertia updates and solves in FP64; same bars, and inverse-dynamics
+    outputs identical to the default call (the flag touches only forward
+    dynamics)."""
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 600, 4, 90, "float32", seed=21,
+                                                fd_fraction=0.4)
+    out = cuda_lib.fleet_batch(plan, *dev, schedule=schedule | cuda_lib.RD_FLEET_FP64_UPDATE)
+    out = out.cpu().numpy()
+    check(reqs, plan, kinds, host, out.astype(np.float64), "float32")
+    ref = cuda_lib.fleet_batch(plan, *dev, schedule=schedule).cpu().numpy()
+    id_mask = np.repeat(kinds, plan.lengths) == 0
+    assert np.array_equal(out[id_mask], ref[id_mask])
+    # the two update precisions agree to far below the FP32 bar
+    fd = ~id_mask
+    scale = np.max(np.abs(ref[fd]))
+    assert np.max(np.abs(out[fd] - ref[fd])) <= 1e-4 * scale
