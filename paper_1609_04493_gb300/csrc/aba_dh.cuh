@@ -1,10 +1,12 @@
 // aba_dh.cuh -- forward dynamics by the articulated-body algorithm (aba.cuh:
 // Sec. II-B, Eqs. abi and recursive-fd) in the common-normal frames of
-// spatial_dh.cuh, with the link constants passed as a __grid_constant__
-// kernel parameter.
+// spatial_dh.cuh. aba_dh_kernel takes the link constants as a __grid_constant__
+// kernel parameter (n % 4 == 0, n <= NMAX, 16-byte aligned rows);
+// aba_dhg_kernel reads them from global memory (any n, any rows; FP32 data);
+// fleets call the same per-instance body.
 //
 // The sweeps and the precision split are those of aba.cuh. What changes is the
-// FP64 articulated-inertia update
+// articulated-inertia update
 //     J_hat_i = J_i + X^T P X,   P = J_hat_{i+1} - U U^T / Omega_{i+1},
 //     X = Ad_{f_{i+1}^-1},  f = (Rx(alpha) Rz(theta), b):
 // * P S = U - U (U^T S) / Omega = 0 for S = e_z (angular), so P has a zero w_z
@@ -18,12 +20,11 @@
 //   xy part.
 // * Then the shift by b, as in aba.cuh.
 // J_i about the frame origin is precomputed on the host (FP64 record below).
-// For n % 4 == 0, n <= NMAX and 16-byte aligned rows.
 //
 // The scalar D of the inertia update and the solves is double, or for FP32
-// data optionally the double-float pair of df.cuh (about 48 bits, computed on
-// the FP32 pipe): the records then hold each FP64 constant split into a pair
-// on the host, and the z_hat / lambda recursions run in D too.
+// data (the default there) the double-float pair of df.cuh (about 48 bits,
+// computed on the FP32 pipe): the records then hold each FP64 constant split
+// into a pair on the host, and the z_hat / lambda recursions run in D too.
 #pragma once
 #include <type_traits>
 
