@@ -112,13 +112,15 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
-    p.add_argument("--kernel-only", choices=["f32", "f64", "f64df", "host", "vjp", "aba", "fleet"],
+    p.add_argument("--kernel-only",
+                   choices=["f32", "f64", "f64df", "host", "vjp", "aba", "aba64", "fleet"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
                         "arithmetic; host: rnea_batch_host on pinned FP32 arrays, the same "
                         "size; vjp: adjoint n=32 B=8192; "
-                        "aba: forward dynamics n=64 B=16384; fleet: 20000 mixed requests)")
+                        "aba: forward dynamics n=64 B=16384 (double-float updates; aba64: "
+                        "FP64 updates); fleet: 20000 mixed requests)")
     return p.parse_args()
 
 
@@ -743,13 +745,15 @@ def run_kernel_only(args):
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]
         for _ in range(calls):
             res = rd.rnea_vjp(model, *x, mode=rd.RD_VJP_RECOMPUTE)[0]
-    elif args.kernel_only == "aba":
+    elif args.kernel_only in ("aba", "aba64"):
+        flags = rd.RD_ABA_FP64_UPDATE if args.kernel_only == "aba64" else 0
         model = rd.Model(chaingen.make_chain(64, seed=chaingen.BASE_SEED))
         st = chaingen.make_states(16384, 64, seed=6000, kinds=("q", "qd", "tau"))
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
-        ws = torch.empty(rd.aba_workspace_bytes(model, 16384, 0), dtype=torch.uint8, device=dev)
+        ws = torch.empty(rd.aba_workspace_bytes(model, 16384, 0, flags), dtype=torch.uint8,
+                         device=dev)
         for _ in range(calls):
-            res = rd.aba(model, *x, workspace=ws)
+            res = rd.aba(model, *x, workspace=ws, flags=flags)
     else:
         count = 20000
         reqs = chaingen.uneven_requests(count, 6, 100, 0.2, seed=chaingen.BASE_SEED)
