@@ -125,7 +125,7 @@ __device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, con
     // shift by b (aba.cuh): A' = A_r, B' = B_r - A_r [b],
     // C' = C_r + [b]B_r - B_r^T[b] - [b]A_r[b]; then + J_i (A = m I, Bm = -[m c], C = C_o)
     const D b[3] = {r[2], r[3], r[4]};
-    D Ar[9], Pm[9], PT[9], Nr[9], Q2[9];
+    D Ar[9], Pm[9], PT[9], Nr[9];
     sym_to_full(M.A, Ar);
     hat_mul(b, Ar, Pm);  // [b] A_r; its transpose is -A_r [b]
 #pragma unroll
@@ -133,7 +133,15 @@ __device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, con
 #pragma unroll
         for (int j = 0; j < 3; ++j) PT[3 * i + j] = Pm[3 * j + i];
     hat_mul(b, M.Bm, Nr);  // [b] B_r
-    hat_mul(b, PT, Q2);    // -[b] A_r [b]
+    // -[b] A_r [b] = [b] PT is symmetric: only its upper triangle is formed
+    // (row 0 of [b] X: b1 X_2j - b2 X_1j; row 1: b2 X_0j - b0 X_2j; row 2:
+    // b0 X_1j - b1 X_0j)
+    const D q00 = fma(b[1], PT[6], -b[2] * PT[3]);
+    const D q01 = fma(b[1], PT[7], -b[2] * PT[4]);
+    const D q02 = fma(b[1], PT[8], -b[2] * PT[5]);
+    const D q11 = fma(b[2], PT[1], -b[0] * PT[7]);
+    const D q12 = fma(b[2], PT[2], -b[0] * PT[8]);
+    const D q22 = fma(b[0], PT[5], -b[1] * PT[2]);
     const D m = ri[6], mcx = ri[16], mcy = ri[17], mcz = ri[18];
     AbiT<D> o;
     o.A = Sym3<D>{M.A.xx + m, M.A.yy + m, M.A.zz + m, M.A.xy, M.A.xz, M.A.yz};
@@ -146,12 +154,12 @@ __device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, con
     o.Bm[6] = M.Bm[6] + PT[6] + mcy;
     o.Bm[7] = M.Bm[7] + PT[7] - mcx;
     o.Bm[8] = M.Bm[8] + PT[8];
-    o.C.xx = M.C.xx + dtwice(Nr[0]) + Q2[0] + ri[19];
-    o.C.yy = M.C.yy + dtwice(Nr[4]) + Q2[4] + ri[20];
-    o.C.zz = M.C.zz + dtwice(Nr[8]) + Q2[8] + ri[21];
-    o.C.xy = M.C.xy + Nr[1] + Nr[3] + dhalf(Q2[1] + Q2[3]) + ri[22];
-    o.C.xz = M.C.xz + Nr[2] + Nr[6] + dhalf(Q2[2] + Q2[6]) + ri[23];
-    o.C.yz = M.C.yz + Nr[5] + Nr[7] + dhalf(Q2[5] + Q2[7]) + ri[24];
+    o.C.xx = dtwice_add(Nr[0], M.C.xx) + q00 + ri[19];
+    o.C.yy = dtwice_add(Nr[4], M.C.yy) + q11 + ri[20];
+    o.C.zz = dtwice_add(Nr[8], M.C.zz) + q22 + ri[21];
+    o.C.xy = M.C.xy + Nr[1] + Nr[3] + q01 + ri[22];
+    o.C.xz = M.C.xz + Nr[2] + Nr[6] + q02 + ri[23];
+    o.C.yz = M.C.yz + Nr[5] + Nr[7] + q12 + ri[24];
     return o;
 }
 

@@ -88,6 +88,9 @@ __device__ __forceinline__ double dhalf(double x) { return 0.5 * x; }
 __device__ __forceinline__ DF dhalf(DF x) { return DF(0.5f * x.hi, 0.5f * x.lo); }
 __device__ __forceinline__ double dtwice(double x) { return 2.0 * x; }
 __device__ __forceinline__ DF dtwice(DF x) { return DF(2.0f * x.hi, 2.0f * x.lo); }
+// 2 x + y: one FMA in double; the exact doubling and one sum in double-float
+__device__ __forceinline__ double dtwice_add(double x, double y) { return fma(2.0, x, y); }
+__device__ __forceinline__ DF dtwice_add(DF x, DF y) { return dtwice(x) + y; }
 
 // 1 / x. DF: the FP32 reciprocal r refined by one Newton step
 // r + r (1 - x r), which doubles its correct bits.
