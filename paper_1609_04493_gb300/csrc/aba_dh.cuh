@@ -274,13 +274,21 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
             Jh = aba_dh_update(P, cn, sn, sd + (i + 1) * kAbaDh64, ri);
             // z_hat_i = X^T (z_hat_{i+1} + U_{i+1} c_hat_{i+1})
             Wrench<Z> zz;
-            zz.f = mk3(z.f.x + dcvt<Z>(Uv[0] * chat), z.f.y + dcvt<Z>(Uv[1] * chat),
-                       z.f.z + dcvt<Z>(Uv[2] * chat));
-            zz.n = mk3(z.n.x + dcvt<Z>(Uw[0] * chat), z.n.y + dcvt<Z>(Uw[1] * chat),
-                       z.n.z + dcvt<Z>(Uw[2] * chat));
-            Wrench<Z> zero;
-            zero.f = zero.n = mk3(Z(0), Z(0), Z(0));
-            z = dh_carry(RnZ, bnZ, zz, zero);
+            if constexpr (kZrec) {  // one fused multiply-add per component
+                zz.f = mk3(fma(Uv[0], chat, z.f.x), fma(Uv[1], chat, z.f.y),
+                           fma(Uv[2], chat, z.f.z));
+                zz.n = mk3(fma(Uw[0], chat, z.n.x), fma(Uw[1], chat, z.n.y),
+                           fma(Uw[2], chat, z.n.z));
+            } else {
+                zz.f = mk3(z.f.x + dcvt<Z>(Uv[0] * chat), z.f.y + dcvt<Z>(Uv[1] * chat),
+                           z.f.z + dcvt<Z>(Uv[2] * chat));
+                zz.n = mk3(z.n.x + dcvt<Z>(Uw[0] * chat), z.n.y + dcvt<Z>(Uw[1] * chat),
+                           z.n.z + dcvt<Z>(Uw[2] * chat));
+            }
+            // z_hat_i = Ad^T zz: the carry of spatial_dh.cuh without a wrench to add
+            // (adding zeros is not an identity in IEEE arithmetic, so it would run)
+            z.f = dh_mul(RnZ, zz.f);
+            z.n = cross_add(bnZ, z.f, dh_mul(RnZ, zz.n));
         }
         const D tau_hat = dsub_exact<D>(tau_i, F.n.z);
         Uv[0] = Jh.Bm[2]; Uv[1] = Jh.Bm[5]; Uv[2] = Jh.Bm[8];
@@ -352,7 +360,7 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
         ua = fma(dcvt<D>(uw.x), dcvt<D>(aw.x), ua);
         ua = fma(dcvt<D>(uw.y), dcvt<D>(aw.y), ua);
         ua = fma(dcvt<D>(uw.z), dcvt<D>(aw.z), ua);
-        const D qdd_i = dcvt<D>(ch) - dcvt<D>(iom) * ua;
+        const D qdd_i = fma(-dcvt<D>(iom), ua, dcvt<D>(ch));
         aw.z = aw.z + dcvt<Z>(qdd_i);
         lv = av;
         lw = aw;
