@@ -58,8 +58,8 @@ enum rd_status {
  * (FP32 for RD_F32) instead of the precision of the articulated-inertia update
  * (FP64 or double-float), which the update and the Omega solves keep. */
 #define RD_ABA_SCANS_IN_DTYPE 0x1
-/* aba_batch flag: run the joint-frame kernel even where the common-normal one
- * applies (n % 4 == 0, n <= 64, 16-byte aligned rows), for comparisons. */
+/* aba_batch flag: run the joint-frame kernel (full 6x6 congruence, FP64 update)
+ * instead of the common-normal ones, for comparisons. */
 #define RD_ABA_JOINT_FRAMES 0x2
 /* aba_batch flag, RD_F32 only. By default the articulated-inertia update, the
  * Omega solves and the z_hat / lambda recursions of FP32 data run in
@@ -67,7 +67,7 @@ enum rd_status {
  * about 48 significand bits; Dekker 1971) on the FP32 pipe, in common-normal
  * frames (constants as a kernel parameter for n % 4 == 0, n <= 64 and aligned
  * rows; in global memory otherwise). This flag runs them in hardware FP64
- * instead. Ignored for RD_F64. */
+ * instead, in the same frames. Ignored for RD_F64. */
 #define RD_ABA_FP64_UPDATE 0x4
 
 /* Per-instance status word of aba_batch (0 = fine). */

@@ -2,8 +2,8 @@
 // Sec. II-B, Eqs. abi and recursive-fd) in the common-normal frames of
 // spatial_dh.cuh. aba_dh_kernel takes the link constants as a __grid_constant__
 // kernel parameter (n % 4 == 0, n <= NMAX, 16-byte aligned rows);
-// aba_dhg_kernel reads them from global memory (any n, any rows; FP32 data);
-// fleets call the same per-instance body.
+// aba_dhg_kernel reads them from global memory (any n, any rows); fleets call
+// the same per-instance body.
 //
 // The sweeps and the precision split are those of aba.cuh. What changes is the
 // articulated-inertia update
@@ -398,22 +398,22 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, D, NMAX> pc, int n, int B,
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }
 
-// Forward dynamics of FP32 data with the constants and the double-float records
-// in global memory, for what the parameter space does not take: chains longer
-// than 64 links, lengths not a multiple of 4, unaligned rows (VEC = false). The
-// sweeps prefetch each next link's constants, records and workspace into L1.
-template <typename Z, int BLOCK, bool VEC>
-__global__ void __launch_bounds__(BLOCK, 384 / BLOCK)
-aba_dhg_kernel(const float *__restrict__ sc, const DF *__restrict__ sd, int n, int B,
-               const float *__restrict__ q, const float *__restrict__ qd,
-               const float *__restrict__ tau, float *__restrict__ qdd_out,
-               int *__restrict__ status, float *__restrict__ ws, Z *__restrict__ wsz,
-               BaseParams<float> base)
+// Forward dynamics with the constants and the records (FP64, or double-float
+// pairs) in global memory, for what the parameter space does not take: chains
+// longer than 64 links, lengths not a multiple of 4, unaligned rows
+// (VEC = false). The sweeps prefetch each next link's constants, records and
+// workspace into L1.
+template <typename T, typename D, typename Z, int BLOCK, bool VEC>
+__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 8 ? 256 : 384) / BLOCK)
+aba_dhg_kernel(const T *__restrict__ sc, const D *__restrict__ sd, int n, int B,
+               const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
+               T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
+               Z *__restrict__ wsz, BaseParams<T> base)
 {
     const int b = blockIdx.x * BLOCK + threadIdx.x;
     if (b >= B) return;
     const size_t row = (size_t)b * (size_t)n;
-    const int bad = aba_dh_instance<float, DF, Z, kTrigPoly, VEC, true>(
+    const int bad = aba_dh_instance<T, D, Z, kTrigPoly, VEC, true>(
         sc, sd, n, q + row, qd + row, tau + row, qdd_out + row, ws, wsz, B, b, base);
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }

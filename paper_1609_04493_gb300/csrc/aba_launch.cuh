@@ -104,7 +104,7 @@ int launch_aba_dh(const rd_model *m, int B, const void *q, const void *qd, const
     return launch_aba_dh_k<T, D, Z, 64, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
 
-template <typename Z, bool VEC>
+template <typename T, typename D, typename Z, bool VEC>
 int launch_aba_dhg(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                    void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
 {
@@ -112,22 +112,36 @@ int launch_aba_dhg(const rd_model *m, int B, const void *q, const void *qd, cons
     const int n = m->n;
     double bb[18];
     rd_convert_base_dh(m, base18, bb);
-    BaseParams<float> bp;
+    BaseParams<T> bp;
     for (int k = 0; k < 6; ++k) {
-        bp.V0[k] = (float)bb[k];
-        bp.dV0[k] = (float)bb[6 + k];
-        bp.Fn[k] = (float)bb[12 + k];
+        bp.V0[k] = (T)bb[k];
+        bp.dV0[k] = (T)bb[6 + k];
+        bp.Fn[k] = (T)bb[12 + k];
     }
-    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(float);
+    const T *sc = nullptr;
+    if constexpr (sizeof(T) == 4) sc = reinterpret_cast<const T *>(m->d_dh32);
+    else sc = reinterpret_cast<const T *>(m->d_dh64);
+    const D *sd = nullptr;
+    if constexpr (std::is_same<D, double>::value) sd = m->d_aba64;
+    else sd = reinterpret_cast<const D *>(m->d_abadf);
+    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
     Z *wsz = reinterpret_cast<Z *>(static_cast<char *>(ws) + ((a + 255) & ~(size_t)255));
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
-    aba_dhg_kernel<Z, BLOCK, VEC><<<grid, BLOCK, 0, stream>>>(
-        m->d_dh32, reinterpret_cast<const DF *>(m->d_abadf), n, B, static_cast<const float *>(q),
-        static_cast<const float *>(qd), static_cast<const float *>(tau), static_cast<float *>(qdd),
-        status, static_cast<float *>(ws), wsz, bp);
+    aba_dhg_kernel<T, D, Z, BLOCK, VEC><<<grid, BLOCK, 0, stream>>>(
+        sc, sd, n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
+        static_cast<const T *>(tau), static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz, bp);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return rd_cuda_fail(e, "aba double-float kernel launch");
+    if (e != cudaSuccess) return rd_cuda_fail(e, "aba global-constant kernel launch");
     return RD_OK;
+}
+
+template <typename T, typename D, typename Z>
+int launch_aba_dhg_v(bool vec, const rd_model *m, int B, const void *q, const void *qd,
+                     const void *tau, void *qdd, int *status, void *ws, const double *base18,
+                     cudaStream_t s)
+{
+    return vec ? launch_aba_dhg<T, D, Z, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+               : launch_aba_dhg<T, D, Z, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
 
 template <typename T>
@@ -155,15 +169,21 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
         }
         return launch_aba_dh<T, double, double>(m, B, q, qd, tau, qdd, status, ws, base18, s);
     }
-    if constexpr (sizeof(T) == 4) {
-        if (!(flags & (RD_ABA_JOINT_FRAMES | RD_ABA_FP64_UPDATE))) {
-            // common-normal frames, constants and double-float records in global memory
+    if (!(flags & RD_ABA_JOINT_FRAMES)) {
+        // common-normal frames, constants and records in global memory
+        if constexpr (sizeof(T) == 4) {
+            if (!(flags & RD_ABA_FP64_UPDATE)) {
+                if (fp32_scans)
+                    return launch_aba_dhg_v<T, DF, T>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
+                return launch_aba_dhg_v<T, DF, DF>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
+            }
             if (fp32_scans)
-                return vec ? launch_aba_dhg<float, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
-                           : launch_aba_dhg<float, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
-            return vec ? launch_aba_dhg<DF, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
-                       : launch_aba_dhg<DF, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+                return launch_aba_dhg_v<T, double, T>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
         }
+        return launch_aba_dhg_v<T, double, double>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
+    }
+    // joint frames (RD_ABA_JOINT_FRAMES), full 6x6 congruence (aba.cuh)
+    if constexpr (sizeof(T) == 4) {
         if (fp32_scans)
             return vec ? launch_aba_k<T, T, 64, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
                        : launch_aba_k<T, T, 64, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);

@@ -25,6 +25,7 @@ struct rd_model {
     double phi_last = 0;      // D_{n-1} is the joint frame of link n turned by phi_last about z
     std::vector<double> host_dh64;  // the common-normal-frame constants on the host
     std::vector<double> host_aba64; // their FP64 forward-dynamics records (aba_dh.cuh)
+    double *d_aba64 = nullptr;      // the records on the device
     float *d_abadf = nullptr;       // the records split into double-float pairs (hi, lo)
     std::vector<double> host_c64;
     // device staging for the host-pointer entry points, grown on demand

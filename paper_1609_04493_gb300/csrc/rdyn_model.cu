@@ -402,6 +402,10 @@ extern "C" int rd_model_create(int n, const double *M, const double *S, const do
         abadf[2 * k] = (float)v;
         abadf[2 * k + 1] = (float)(v - (double)(float)v);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&mdl->d_aba64, mdl->host_aba64.size() * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(mdl->d_aba64, mdl->host_aba64.data(), mdl->host_aba64.size() * sizeof(double),
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&mdl->d_abadf, abadf.size() * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMemcpy(mdl->d_abadf, abadf.data(), abadf.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -425,6 +429,7 @@ extern "C" void rd_model_destroy(rd_model *m)
     if (m->d_c64) cudaFree(m->d_c64);
     if (m->d_dh32) cudaFree(m->d_dh32);
     if (m->d_dh64) cudaFree(m->d_dh64);
+    if (m->d_aba64) cudaFree(m->d_aba64);
     if (m->d_abadf) cudaFree(m->d_abadf);
     if (m->d_io) cudaFree(m->d_io);
     if (m->io_in) cudaStreamDestroy(m->io_in);

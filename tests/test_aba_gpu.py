@@ -263,13 +263,13 @@ def test_aba_long_chain_n128(cuda_lib):
     1e-3 * n / 64: the error grows along the chain with the FP32 bias sweeps
     (tau_hat = tau - tau_bias cancels against bias torques far above tau), which
     the precision of the inertia update does not change; the FP64-update path
-    (joint frames beyond 64 links) is printed beside it."""
+    is printed beside it."""
     n = 128
     a, ch, h, _ = run(cuda_lib, n, 400, "float32", seed=59)
     b, _, _, _ = run(cuda_lib, n, 400, "float32", seed=59, flags=cuda_lib.RD_ABA_FP64_UPDATE)
     ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
     ea, eb = oracle.rel_err(a, ref), oracle.rel_err(b, ref)
-    print(f"n = 128 FP32: double-float update {ea:.3e}, FP64 update (joint frames) {eb:.3e}")
+    print(f"n = 128 FP32: double-float update {ea:.3e}, FP64 update {eb:.3e}")
     assert ea <= TOL["float32"] * n / 64
     assert eb <= TOL["float32"] * n / 64
 
@@ -310,3 +310,23 @@ def test_aba_global_constant_kernel_full_batch_n100(cuda_lib):
     scale = np.maximum(np.max(np.abs(h["tau"][idx]), axis=1), np.max(np.abs(bias), axis=1))
     err = np.max(np.abs(back - h["tau"][idx]), axis=1) / scale
     assert err.max() <= 1e-4 * n / 16, err.max()
+
+
+@pytest.mark.parametrize("dtype,flags", [("float64", 0), ("float32", 4)])
+def test_aba_global_constant_kernel_fp64_update_agrees_with_joint_frames(cuda_lib, dtype, flags):
+    """n = 100: the common-normal kernel with constants and FP64 records in
+    global memory (FP64 data; FP32 data with RD_ABA_FP64_UPDATE) against the
+    joint-frame kernel on the same data (FP64: one result to rounding; FP32:
+    each against the oracle on the bar scaled by n / 64 of
+    test_aba_long_chain_n128, since the FP32 sweeps round differently in the
+    two frames)."""
+    n = 100
+    a, ch, h, _ = run(cuda_lib, n, 300, dtype, seed=83, flags=flags)
+    b, _, _, _ = run(cuda_lib, n, 300, dtype, seed=83, flags=flags | cuda_lib.RD_ABA_JOINT_FRAMES)
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"], base=None)
+    if dtype == "float64":
+        assert oracle.rel_err(a, b) <= 1e-9
+        assert oracle.rel_err(a, ref) <= TOL[dtype]
+    else:
+        assert oracle.rel_err(a, ref) <= TOL[dtype] * n / 64
+        assert oracle.rel_err(b, ref) <= TOL[dtype] * n / 64
