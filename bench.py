@@ -88,9 +88,9 @@ FD_EXEC_FLOP32_PER_LINK = 257
 FD_EXEC_FLOP64_PER_LINK = 400
 # the default for FP32 data carries those FP64 operations in double-float
 # arithmetic on the FP32 pipe: FP32-pipe instructions executed per link, from
-# the FMA-pipe count of an ncu capture at n = 64, B = 16384 (105.4 M warp
+# the FMA-pipe count of an ncu capture at n = 64, B = 16384 (99.7 M warp
 # instructions, 94% of all)
-FD_DF_EXEC_FP32_INST_PER_LINK = 3217
+FD_DF_EXEC_FP32_INST_PER_LINK = 3043
 # FP32-pipe instructions per link of the double-float kernel for FP64 data
 # (RD_VARIANT_SERIAL_DF), from the FMA-pipe count of an ncu capture at n = 32,
 # B = 65536 (166.2 M warp instructions, 92% of all)
