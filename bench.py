@@ -397,6 +397,50 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
     return out
 
 
+def crossover_section(torch, rd, chaingen, dev, dist, sampler, K):
+    """The inverse-dynamics workload's other sizes: n = 16 and 100 at the same
+    batch (AUTO), and the lane-parallel scan against the serial recursion at
+    n = 32 across small batches."""
+    out = {}
+
+    def case(n, B, variant):
+        model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
+        sets = []
+        for r in range(4):
+            st = chaingen.make_states(B, n, seed=8000 + r)
+            sets.append([torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd")])
+        o = torch.empty_like(sets[0][0])
+        steps = max(3, min(K, 100))
+
+        def call(k):
+            rd.rnea(model, *sets[k % len(sets)], out=o, variant=variant)
+
+        t = time_calls(torch, call, steps, 3, dist, sampler)
+        return t / steps, rd.rnea_last_config()
+
+    for n in (16, 100):
+        t, fam = case(n, BATCH, rd.RD_VARIANT_AUTO)
+        out[f"n{n}_B{BATCH}"] = {
+            "value": BATCH / t, "unit": UNIT, "ms_per_step": t * 1e3, "kernel_family": fam[0],
+            "stored_links": fam[2],
+            "algorithmic_frac_of_fp32_peak":
+                BATCH * n * ALGO_FLOP_PER_LINK / t / (fp32_peak_tflops() * 1e12)}
+    for B in (1024, 2048, 4096, 8192):
+        row = {}
+        for name, v in (("auto", rd.RD_VARIANT_AUTO), ("serial", rd.RD_VARIANT_SERIAL_DH),
+                        ("scan16", rd.RD_VARIANT_SCAN(16))):
+            t, fam = case(N_LINKS, B, v)
+            row[name] = t * 1e6
+            if name == "auto":
+                row["auto_kernel_family"] = fam[0]
+        out[f"n{N_LINKS}_B{B}_us"] = row
+    out["metric"] = ("RNEA FP32: evals/s at n = 16 and 100 (B = 65536, AUTO); microseconds per "
+                     "call at n = 32 for small B: AUTO, the serial common-normal recursion and the "
+                     "16-lane scan")
+    out["inputs"] = "4 input sets rotated; the small batches are L2-resident, as they are in use"
+    return out
+
+
 def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
     from paper_1609_04493_gb300 import autotune
 
@@ -631,6 +675,8 @@ def run_ours(args):
         res["adjoint"] = adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K)
         # ---- forward dynamics (aba_batch), n = 16 and 64, B = 16384 FP32
         res["forward_dynamics"] = fd_section(torch, rd, chaingen, dev, dist, sampler, K)
+        # ---- the inverse-dynamics workload's other sizes and the scan / serial crossover
+        res["crossover"] = crossover_section(torch, rd, chaingen, dev, dist, sampler, K)
         # ---- uneven batching: 100000 mixed requests (fleet_batch)
         if not args.no_uneven:
             res["uneven"] = uneven_section(torch, rd, chaingen, dev, dist, sampler, K)
