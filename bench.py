@@ -343,6 +343,14 @@ def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
                      "frac_of_fp32_peak": tx / peak32,
                      "algorithmic_flop_per_link": VJP_ALGO_FLOP_PER_LINK,
                      "algorithmic_tflops": tf, "algorithmic_frac_of_fp32_peak": tf / peak32}
+        if B == 8192 and mode == rd.RD_VJP_RECOMPUTE:
+            # each instance split between two warps (RD_VJP_FLAG_TWO_WARPS)
+            def call2(k):
+                x, o = sets[k % len(sets)]
+                rd.rnea_vjp(model, *x, mode=mode | rd.RD_VJP_FLAG_TWO_WARPS, out=o)
+
+            t2 = time_calls(torch, call2, steps, 3, dist, sampler)
+            out[name]["two_warps"] = {"value": B * steps / t2, "ms_per_step": t2 / steps * 1e3}
     out["metric"] = "RNEA adjoint d(w^T tau)/d(q, qd, qdd) evals/s, n=32 FP32"
     return out
 

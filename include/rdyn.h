@@ -226,6 +226,14 @@ enum rd_vjp_mode {
 /* OR-able into the mode of rnea_vjp: run the joint-frame kernel even where the
  * common-normal one applies (for comparisons). */
 #define RD_VJP_FLAG_JOINT_FRAMES 0x2000
+/* OR-able into the mode of rnea_vjp, for FP32 in RD_VJP_RECOMPUTE on
+ * common-normal rows: split each instance between two warps, one carrying the
+ * motion and the wrenches, the other the adjoints (RD_VJP_FLAG_TWO_WARPS), or
+ * keep one thread per instance (RD_VJP_FLAG_ONE_THREAD). Without either, the
+ * library splits chains of more than 64 links in batches of at most 8192
+ * states, the case where the split measured faster. Setting both is RD_ERR_ARG. */
+#define RD_VJP_FLAG_TWO_WARPS 0x800
+#define RD_VJP_FLAG_ONE_THREAD 0x400
 
 /*
  * rnea_vjp -- vector-Jacobian product of inverse dynamics for B states:

@@ -31,6 +31,8 @@ RD_VJP_AUTO = 0
 RD_VJP_STORE = 1
 RD_VJP_RECOMPUTE = 2
 RD_VJP_FLAG_JOINT_FRAMES = 0x2000
+RD_VJP_FLAG_TWO_WARPS = 0x800
+RD_VJP_FLAG_ONE_THREAD = 0x400
 
 
 def RD_VARIANT_SCAN(lanes):

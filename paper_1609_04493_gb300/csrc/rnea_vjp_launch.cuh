@@ -9,6 +9,7 @@
 #include "rdyn_internal.h"
 #include "rnea_vjp.cuh"
 #include "rnea_vjp_dh.cuh"
+#include "rnea_vjp_pair.cuh"
 
 namespace rdyn {
 namespace {
@@ -101,11 +102,49 @@ int launch_vjp_dh_k(const rd_model *m, int B, const void *q, const void *qd, con
     return RD_OK;
 }
 
+template <int NMAX, int TRIG>
+int launch_vjp_pair_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                      const void *w, void *gq, void *gqd, void *gqdd, const double *base18,
+                      cudaStream_t stream)
+{
+    double b[18];
+    rd_convert_base_dh(m, base18, b);
+    BaseParams<float> bp;
+    for (int k = 0; k < 6; ++k) {
+        bp.V0[k] = (float)b[k];
+        bp.dV0[k] = (float)b[6 + k];
+        bp.Fn[k] = (float)b[12 + k];
+    }
+    DhParamConsts<float, NMAX> pc;
+    for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (float)m->host_dh64[k];
+    for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = 0.0f;
+    const unsigned grid = (unsigned)((B + 31) / 32);
+    rnea_vjp_pair_kernel<NMAX, TRIG><<<grid, 64, 0, stream>>>(
+        pc, m->n, B, static_cast<const float *>(q), static_cast<const float *>(qd),
+        static_cast<const float *>(qdd), static_cast<const float *>(w), static_cast<float *>(gq),
+        static_cast<float *>(gqd), static_cast<float *>(gqdd), bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_vjp two-warp kernel launch");
+    return RD_OK;
+}
+
+// split: > 0 two warps per instance, < 0 one thread, 0 the library's choice
 template <typename T, int MODE, int TRIG>
 int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                   const void *w, void *gq, void *gqd, void *gqdd, void *ws,
-                  const double *base18, cudaStream_t s)
+                  const double *base18, int split, cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4 && MODE == kVjpRecompute) {
+        // CUDA-graph timings: n = 100, B = 8192: 40.6 us split, 44.8 one thread;
+        // n = 32, B = 8192: 13.2 vs 12.8; n = 16: 7.9 vs 6.9. A small batch takes
+        // the latency of one instance's motion and wrench recursion, which the
+        // split leaves on one warp; only long chains gain.
+        if (split > 0 || (split == 0 && m->n > 64 && B <= 8192)) {
+            if (m->n <= 32)
+                return launch_vjp_pair_k<32, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
+            return launch_vjp_pair_k<128, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
+        }
+    }
     // small batches: 32-thread blocks spread the few warps over more SMs
     const bool small = B <= 152 * 128;
     if (m->n <= 32)
@@ -120,15 +159,18 @@ int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const
 template <typename T, int MODE>
 int launch_vjp_any(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    const void *w, void *gq, void *gqd, void *gqdd, void *ws,
-                   const double *base18, bool fast, bool joint_frames, cudaStream_t s)
+                   const double *base18, bool fast, bool joint_frames, int split,
+                   cudaStream_t s)
 {
     const bool dh = !joint_frames && m->n % 4 == 0 && m->n <= 128 && vjp_aligned16(q) &&
                     vjp_aligned16(qd) && vjp_aligned16(qdd) && vjp_aligned16(w) &&
                     vjp_aligned16(gq) && vjp_aligned16(gqd) && vjp_aligned16(gqdd);
     if (dh) {
         if (sizeof(T) == 4 && fast)
-            return launch_vjp_dh<T, MODE, kTrigSfu>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
-        return launch_vjp_dh<T, MODE, kTrigPoly>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, s);
+            return launch_vjp_dh<T, MODE, kTrigSfu>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18,
+                                                    split, s);
+        return launch_vjp_dh<T, MODE, kTrigPoly>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18,
+                                                 split, s);
     }
     return launch_vjp_mode<T, MODE>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast, s);
 }
@@ -140,6 +182,9 @@ int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
 {
     const bool fast = (mode & RD_FLAG_FAST_TRIG) != 0;
     const bool joint_frames = (mode & RD_VJP_FLAG_JOINT_FRAMES) != 0;
+    if ((mode & RD_VJP_FLAG_TWO_WARPS) && (mode & RD_VJP_FLAG_ONE_THREAD))
+        return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_TWO_WARPS and RD_VJP_FLAG_ONE_THREAD both set");
+    const int split = (mode & RD_VJP_FLAG_TWO_WARPS) ? 1 : (mode & RD_VJP_FLAG_ONE_THREAD) ? -1 : 0;
     mode &= 0xff;
     const size_t need = (size_t)m->n * kVjpStateScalars * (size_t)B * sizeof(T);
     if (mode == RD_VJP_AUTO) {
@@ -154,11 +199,11 @@ int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
                            need, ws_bytes);
         if (!vjp_aligned16(ws)) return rd_fail(RD_ERR_ARG, "rnea_vjp: workspace not 16-byte aligned");
         return launch_vjp_any<T, kVjpStore>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast,
-                                            joint_frames, s);
+                                            joint_frames, split, s);
     }
     if (mode == RD_VJP_RECOMPUTE)
         return launch_vjp_any<T, kVjpRecompute>(m, B, q, qd, qdd, w, gq, gqd, gqdd, nullptr,
-                                                base18, fast, joint_frames, s);
+                                                base18, fast, joint_frames, split, s);
     return rd_fail(RD_ERR_ARG, "rnea_vjp: unknown mode %d", mode);
 }
 

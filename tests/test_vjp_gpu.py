@@ -188,3 +188,66 @@ def test_vjp_recompute_large_batch_sampled(cuda_lib):
     idx = np.arange(0, B, 512)
     ref = oracle.rnea_grad(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd", "w")))
     assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+
+
+# ---- FP32 recompute with each instance split between two warps
+
+@pytest.mark.parametrize("B", [1, 31, 33, 150])
+@pytest.mark.parametrize("n", [4, 8, 32, 64, 100, 128])
+def test_vjp_two_warps_match_complex_step(cuda_lib, n, B):
+    mode = cuda_lib.RD_VJP_RECOMPUTE | cuda_lib.RD_VJP_FLAG_TWO_WARPS
+    g, ref, _, _ = run(cuda_lib, n, B, "float32", mode, seed=19)
+    err = grad_err(g, ref)
+    assert err <= TOL["float32"], f"n={n} B={B}: {err:.3e}"
+
+
+def test_vjp_two_warps_agree_with_one_thread(cuda_lib):
+    """The split kernel and the one-thread kernel evaluate the same formulas."""
+    rec = cuda_lib.RD_VJP_RECOMPUTE
+    for n in (16, 32):
+        a, ref, _, _ = run(cuda_lib, n, 3000, "float32", rec | cuda_lib.RD_VJP_FLAG_TWO_WARPS, seed=21)
+        b, _, _, _ = run(cuda_lib, n, 3000, "float32", rec | cuda_lib.RD_VJP_FLAG_ONE_THREAD, seed=21)
+        assert grad_err(a, ref) <= TOL["float32"] and grad_err(b, ref) <= TOL["float32"]
+        assert grad_err(a, b) <= 1e-4
+
+
+def test_vjp_two_warps_base_motion_wrench_and_fast_trig(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    mode = cuda_lib.RD_VJP_RECOMPUTE | cuda_lib.RD_VJP_FLAG_TWO_WARPS
+    g, ref, _, _ = run(cuda_lib, 8, 70, "float32", mode, base=base, seed=23)
+    assert grad_err(g, ref) <= TOL["float32"]
+    g, ref, _, _ = run(cuda_lib, 32, 200, "float32", mode | cuda_lib.RD_FLAG_FAST_TRIG, seed=17)
+    assert grad_err(g, ref) <= TOL["float32"]
+
+
+@pytest.mark.parametrize("n, flag", [(32, "two"), (100, "auto")])
+def test_vjp_two_warps_full_workload_sampled(cuda_lib, n, flag):
+    """B = 8192 FP32 recompute split over two warps: forced at n = 32 (the
+    adjoint workload's size), the library's own choice at n = 100. Every 32nd
+    instance against the oracle."""
+    import torch
+
+    B = 8192
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=5000, kinds=("q", "qd", "qdd", "w"))
+    host = {k: st[k].astype(np.float32) for k in st}
+    dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
+    mode = cuda_lib.RD_VJP_RECOMPUTE
+    if flag == "two":
+        mode |= cuda_lib.RD_VJP_FLAG_TWO_WARPS
+    g = cuda_lib.rnea_vjp(cuda_lib.Model(ch), dev["q"], dev["qd"], dev["qdd"], dev["w"], mode=mode)
+    idx = np.arange(0, B, 32)
+    ref = oracle.rnea_grad(ch, *(host[k][idx].astype(np.float64) for k in ("q", "qd", "qdd", "w")))
+    assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+
+
+def test_vjp_split_flags_conflict(cuda_lib):
+    import torch
+
+    x = torch.zeros(4, 8, device="cuda")
+    model = cuda_lib.Model(chaingen.make_chain(8, seed=3))
+    mode = (cuda_lib.RD_VJP_RECOMPUTE | cuda_lib.RD_VJP_FLAG_TWO_WARPS |
+            cuda_lib.RD_VJP_FLAG_ONE_THREAD)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(model, x, x, x, x, mode=mode)
