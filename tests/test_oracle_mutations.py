@@ -89,7 +89,22 @@ def check_gradient():
     return True
 
 
-CHECKS = [check_pendulum, check_lagrange, check_external_wrench, check_fd, check_gradient]
+def check_abi_schur():
+    ch = _chain(4)
+    q = chaingen.make_states(1, 4, seed=43, kinds=("q",))["q"][0]
+    _, Om = oracle.abi_trace(ch, q)
+    Mq = L.mass_matrix(ch, q)
+    for i in range(4):
+        a = Mq[i, i]
+        if i + 1 < 4:
+            a -= Mq[i + 1:, i] @ np.linalg.solve(Mq[i + 1:, i + 1:], Mq[i + 1:, i])
+        if not abs(Om[i] - a) <= 1e-9 * Mq[i, i]:
+            return False
+    return True
+
+
+CHECKS = [check_pendulum, check_lagrange, check_external_wrench, check_fd, check_gradient,
+          check_abi_schur]
 
 MUTATIONS = {
     "drop_coriolis_ad_term": {"dyn_body.h": [

@@ -346,6 +346,24 @@ def test_abi_tip_and_omega():
         assert abs(ch.S[i] @ Jh[i] @ ch.S[i] - Om[i]) < 1e-12
 
 
+@pytest.mark.parametrize("n", [1, 2, 5, 9])
+def test_abi_omega_is_the_schur_complement_of_the_mass_matrix(n):
+    """Omega_i of Eq. (abi) is the inertia joint i feels with the joints above it
+    free and those below it locked: the Schur complement of M[i+1:, i+1:] in
+    M[i:, i:] (the pivots of M's factorisation eliminated tip first). M(q) comes
+    from unit-acceleration IDs, pinned against the Lagrangian restatement."""
+    ch = chain_n(n)
+    for q in states(3, n)["q"]:
+        _, Om = oracle.abi_trace(ch, q)
+        Mq = oracle.mass_matrix(ch, q)[0]
+        for i in range(n):
+            a = Mq[i, i]
+            if i + 1 < n:
+                c = Mq[i + 1:, i]
+                a -= c @ np.linalg.solve(Mq[i + 1:, i + 1:], c)
+            assert abs(Om[i] - a) <= 1e-11 * Mq[i, i], (n, i, Om[i], a)
+
+
 def test_fd_single_link_closed_form():
     m, l, Ixx = 1.7, 0.45, 0.03
     ch = chaingen.pendulum(m, l, Ixx)
