@@ -19,8 +19,8 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char|double|float)\s*\**\s*(\w+)\s*\(",
-                             text, flags=re.M):
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:long\s+long|size_t|int|void|char|double|float)"
+                             r"\s*\**\s*(\w+)\s*\(", text, flags=re.M):
             names.add(m.group(1))
     return sorted(names)
 
@@ -35,7 +35,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("rd_model_create", "rd_model_destroy", "rnea_batch", "rnea_batch_host",
-                     "rd_last_error", "rd_version"):
+                     "rnea_vjp", "aba_batch", "jsiia_batch", "fleet_batch",
+                     "rd_plan_total_joints", "rd_last_error", "rd_version"):
         assert required in names
 
 
