@@ -18,7 +18,7 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def cuda_lib():
-    """The product library on a GPU machine; the test fails loudly if it is missing."""
+    """The product library on a CUDA machine; the test fails loudly if it is missing."""
     import torch
 
     if not torch.cuda.is_available():
