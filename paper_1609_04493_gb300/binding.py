@@ -338,6 +338,10 @@ def rnea_vjp(model, q, qd, qdd, w, base=None, mode=RD_VJP_AUTO, workspace=None, 
              out=None):
     """(gq, gqd, gqdd) = d(w^T tau)/d(q, qd, qdd) on the GPU (rnea_vjp).
 
+    ``mode`` is RD_VJP_AUTO, RD_VJP_STORE or RD_VJP_RECOMPUTE, optionally OR-ed
+    with RD_FLAG_FAST_TRIG, RD_VJP_FLAG_JOINT_FRAMES, and for FP32 recompute
+    RD_VJP_FLAG_TWO_WARPS or RD_VJP_FLAG_ONE_THREAD (each instance split between
+    two warps, or not; by default split for chains over 64 links at B <= 8192).
     In store mode (or AUTO with a workspace) the caller may pass a preallocated
     uint8 CUDA tensor as ``workspace``; for RD_VJP_STORE without one, a tensor of
     the required size is allocated here (torch's allocator), never in the library."""
