@@ -192,7 +192,8 @@ int rnea_batch(const rd_model *model, int B, int dtype, const void *q, const voi
                const void *qdd, void *tau, const double *base, int variant, void *stream);
 
 /*
- * rnea_batch_host -- rnea_batch on HOST arrays; returns when tau is on the host.
+ * rnea_batch_host -- rnea_batch on HOST arrays (the inverse dynamics of Sec. II-A,
+ * Eqs. id-forward and id-backward); returns when tau is on the host.
  * In place: with variant RD_VARIANT_AUTO, RD_F32 data, n % 4 == 0, n <= 64 and
  * all four arrays mapped pinned host memory (cudaHostAlloc under unified
  * addressing, as pinned torch tensors are) on 16-byte boundaries, one kernel
@@ -267,9 +268,10 @@ int rnea_vjp_workspace_size(const rd_model *model, int B, int dtype, size_t *byt
 #define RD_VJP_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /*
- * rnea_vjp_noalloc -- rnea_vjp in RD_VJP_STORE mode for callers that cannot
- * allocate device memory when they call (a real-time loop with a
- * no-allocation rule, a plug-in whose host framework owns the memory pool).
+ * rnea_vjp_noalloc -- rnea_vjp (the adjoint of the recursions of Sec. II-A) in
+ * RD_VJP_STORE mode for callers that cannot allocate device memory when they
+ * call (a real-time loop with a no-allocation rule, a plug-in whose host
+ * framework owns the memory pool).
  * This is an interface convenience of the library; the paper has no
  * counterpart.
  *
@@ -368,7 +370,9 @@ int rd_fleet_create(int nrobots, const int *n, const double *M, const double *S,
 void rd_fleet_destroy(rd_fleet *fleet);
 
 /*
- * rd_plan_create -- a fixed set of R requests on a fleet, for data type dtype.
+ * rd_plan_create -- a fixed set of R requests on a fleet, for data type dtype:
+ * the group-level batching of many robots (Sec. I), each request inverse
+ * dynamics (Sec. II-A) or forward dynamics (Sec. II-B).
  *   robot    host int[R]: robot of each request.
  *   kind     host int[R]: RD_REQ_ID (tau from q, qd, qdd) or RD_REQ_FD (qdd from
  *            q, qd, tau; articulated-body algorithm as aba_batch: inertia updates
@@ -391,7 +395,8 @@ int rd_plan_offsets(const rd_plan *plan, long long *off);
 int rd_plan_groups(const rd_plan *plan);
 
 /*
- * fleet_batch -- evaluate every request of a plan.
+ * fleet_batch -- evaluate every request of a plan: tau = ID(q, qd, qdd) of
+ * Sec. II-A or qdd = FD(q, qd, tau) of Sec. II-B (Eqs. abi, recursive-fd).
  *   q, qd    device, ragged inputs (plan dtype).
  *   in2      device: qdd for RD_REQ_ID requests, tau for RD_REQ_FD requests.
  *   out      device: tau for RD_REQ_ID, qdd for RD_REQ_FD; must not alias inputs.
