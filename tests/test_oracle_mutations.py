@@ -142,6 +142,12 @@ MUTATIONS = {
     "aba_lambda_missing_Y": {"oracle_real.c": [
         ("for (int k = 0; k < 6; ++k) lam[k] = lnew[k] + S[6 * i + k] * ch[i];",
          "for (int k = 0; k < 6; ++k) lam[k] = S[6 * i + k] * ch[i];")]},
+    "aba_congruence_not_transposed": {"oracle_real.c": [
+        ("mat6_mul(XT, Jh[i + 1], T1);    /* X^T hat J */",
+         "mat6_mul(X[i + 1], Jh[i + 1], T1);    /* X^T hat J */")]},
+    "abi_trace_rank_one_term_dropped": {"oracle_real.c": [
+        ("Jh[i][a][b2] = J[a][b2] + XTJX[a][b2] - u[a] * u[b2] / Om1;",
+         "Jh[i][a][b2] = J[a][b2] + XTJX[a][b2];")]},
     "jsiia_bias_not_subtracted": {"oracle_real.c": [
         ("double s = tau[o + i] - bias[i];", "double s = tau[o + i];")]},
     "complex_step_reads_real_part": {"oracle_cs.c": [
