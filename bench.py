@@ -98,9 +98,38 @@ RNEA_DF_EXEC_FP32_INST_PER_LINK = 2535
 # bytes an inverse-dynamics link of the uneven workload moves: q, qd, qdd, tau
 # (16) plus its robot's constants streamed per request (112)
 UNEVEN_ID_BYTES_PER_LINK = 128
-SM_COUNT = 152
+# Peaks: FP32 lanes and FP64 fused multiply-adds per SM per clock (GB300:
+# 1.25 TFLOP/s FP64 nominal at 152 SMs and 2.07 GHz). The bench multiplies them
+# by the device's SM count and the median SM clock sampled while it ran.
+SM_COUNT_NOMINAL = 152
+SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
-FP64_NOMINAL_TFLOPS = 1.25
+FP64_FMA_PER_SM_CLK = 2
+
+
+def fp32_peak_tflops(sm_count=SM_COUNT_NOMINAL, mhz=SM_MAX_MHZ):
+    return sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(sm_count=SM_COUNT_NOMINAL, mhz=SM_MAX_MHZ):
+    return sm_count * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+
+
+def fp32_inst_rate(sm_count=SM_COUNT_NOMINAL, mhz=SM_MAX_MHZ):
+    """FP32-pipe thread instructions per second."""
+    return sm_count * FP32_LANES_PER_SM * mhz * 1e6
+
+
+def rnd(x, digits=4):
+    """Round every float in a nested structure to `digits` significant digits
+    (keeps the printed line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}") if x == x and abs(x) != float("inf") else x
+    if isinstance(x, dict):
+        return {k: rnd(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [rnd(v, digits) for v in x]
+    return x
 
 
 def parse_args():
@@ -245,10 +274,6 @@ def kernel_sources_hash(files=RNEA_KERNEL_SOURCES):
     return hs.hexdigest()[:16]
 
 
-def fp32_peak_tflops():
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
-
-
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -313,8 +338,21 @@ def time_calls(torch, fn, steps, warmup, dist, sampler):
     return max_over_ranks(dist, timed_graph(torch, g, dist, sampler))
 
 
+class Peaks:
+    """Roofline denominators for the device and the clock it ran at."""
+
+    def __init__(self, sm_count, mhz):
+        self.sm, self.mhz = sm_count, mhz
+        self.f32 = fp32_peak_tflops(sm_count, mhz) * 1e12  # flop/s
+        self.f64 = fp64_peak_tflops(sm_count, mhz) * 1e12
+        self.i32 = fp32_inst_rate(sm_count, mhz)           # FP32-pipe instructions/s
+        self.hbm = measured_peaks().get("hbm_gbs", 6800.0) * 1e9  # B/s
+
+
 def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
-    out = {}
+    """Seconds per rnea_vjp call at n = 32 FP32: recompute at B = 8192 and
+    262144, store at 8192, and the two-warp split at 8192."""
+    raw = {}
     for B, mode in ((8192, rd.RD_VJP_RECOMPUTE), (262144, rd.RD_VJP_RECOMPUTE),
                     (8192, rd.RD_VJP_STORE)):
         sets = []
@@ -332,31 +370,35 @@ def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
             x, o = sets[k % len(sets)]
             rd.rnea_vjp(model, *x, mode=mode, workspace=ws, out=o)
 
-        t = time_calls(torch, call, steps, 3, dist, sampler)
         name = f"B{B}_{'store' if mode == rd.RD_VJP_STORE else 'recompute'}"
-        fpl = VJP_FLOP_PER_LINK[mode]
-        tf = B * N_LINKS * VJP_ALGO_FLOP_PER_LINK / (t / steps) / 1e12
-        tx = B * N_LINKS * fpl / (t / steps) / 1e12
-        peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
-        out[name] = {"value": B * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3,
-                     "steps": steps, "flop_per_link": fpl, "achieved_tflops": tx,
-                     "frac_of_fp32_peak": tx / peak32,
-                     "algorithmic_flop_per_link": VJP_ALGO_FLOP_PER_LINK,
-                     "algorithmic_tflops": tf, "algorithmic_frac_of_fp32_peak": tf / peak32}
+        raw[name] = {"B": B, "mode": mode,
+                     "t": time_calls(torch, call, steps, 3, dist, sampler) / steps}
         if B == 8192 and mode == rd.RD_VJP_RECOMPUTE:
-            # each instance split between two warps (RD_VJP_FLAG_TWO_WARPS)
             def call2(k):
                 x, o = sets[k % len(sets)]
                 rd.rnea_vjp(model, *x, mode=mode | rd.RD_VJP_FLAG_TWO_WARPS, out=o)
 
-            t2 = time_calls(torch, call2, steps, 3, dist, sampler)
-            out[name]["two_warps"] = {"value": B * steps / t2, "ms_per_step": t2 / steps * 1e3}
-    out["metric"] = "RNEA adjoint d(w^T tau)/d(q, qd, qdd) evals/s, n=32 FP32"
+            raw[name]["t2"] = time_calls(torch, call2, steps, 3, dist, sampler) / steps
+    return raw
+
+
+def adjoint_report(raw, pk):
+    """frac: the kernel's executed arithmetic (FMA = 2) over the FP32 peak."""
+    out = {}
+    for name, r in raw.items():
+        fpl = VJP_FLOP_PER_LINK[r["mode"]]
+        out[name] = {"us": r["t"] * 1e6, "value": r["B"] / r["t"], "flop_per_link": fpl,
+                     "frac": r["B"] * N_LINKS * fpl / r["t"] / pk.f32}
+        if "t2" in r:
+            out[name]["two_warps_us"] = r["t2"] * 1e6
     return out
 
 
 def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
-    out = {}
+    """Seconds per aba_batch call, FP32 data, B = 16384, n = 16 and 64: FP64
+    inertia updates and solves (the workload's precision plan) and the
+    library's double-float default."""
+    raw = {}
     B = 16384
     for n in (16, 64):
         model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
@@ -364,52 +406,45 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
         for r in range(4):
             st = chaingen.make_states(B, n, seed=6000 + r, kinds=("q", "qd", "tau"))
             sets.append([torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")])
-        ws = torch.empty(rd.aba_workspace_bytes(model, B, 0), dtype=torch.uint8, device=dev)
+        nbytes = max(rd.aba_workspace_bytes(model, B, 0),
+                     rd.aba_workspace_bytes(model, B, 0, rd.RD_ABA_FP64_UPDATE))
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         o = torch.empty_like(sets[0][0])
         steps = max(3, min(K, 50))
-        inst_rate = SM_COUNT * FP32_LANES_PER_SM * 2.070e9  # FP32-pipe thread instructions/s
 
         def timed(flags):
             def call(k):
                 x = sets[k % len(sets)]
                 rd.aba(model, *x, workspace=ws, out=o, flags=flags)
-            return time_calls(torch, call, steps, 3, dist, sampler)
+            return time_calls(torch, call, steps, 3, dist, sampler) / steps
 
-        t64 = timed(rd.RD_ABA_FP64_UPDATE)
-        tdf = timed(0)
-        t_exec64 = B * n * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
-                            + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
-        t_floor = B * n * FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12)
-        t_exec = B * n * FD_DF_EXEC_FP32_INST_PER_LINK / inst_rate
-        out[f"n{n}_B{B}"] = {"value": B * steps / t64, "unit": UNIT,
-                             "ms_per_step": t64 / steps * 1e3, "steps": steps,
-                             "roofline_ms": t_exec64 * 1e3,
-                             "roofline_frac": t_exec64 / (t64 / steps),
-                             "fp64_pipe_floor_ms": t_floor * 1e3,
-                             "double_float": {"value": B * steps / tdf,
-                                              "ms_per_step": tdf / steps * 1e3,
-                                              "roofline_ms": t_exec * 1e3,
-                                              "roofline_frac": t_exec / (tdf / steps)}}
-    out["algorithmic_flop_per_link"] = {"fp32": FD_FLOP32_PER_LINK,
-                                         "extended_precision": FD_FLOP64_PER_LINK}
-    out["metric"] = ("forward dynamics (articulated-body, FP32 data, FP64 inertia updates and "
-                     "solves as the workload specifies; beside it the library's default, the "
-                     "same in double-float arithmetic) evals/s")
-    out["roofline"] = (f"FP64 updates: combined FP32 + FP64 time of the kernel's "
-                       f"{FD_EXEC_FLOP32_PER_LINK} FP32 and {FD_EXEC_FLOP64_PER_LINK} FP64 flop "
-                       f"per link at the derived FP32 and nominal FP64 peaks, divided by the "
-                       f"measured time; fp64_pipe_floor_ms: the FP64 part alone; double_float: "
-                       f"FP32-pipe issue time of its {FD_DF_EXEC_FP32_INST_PER_LINK} FP32 "
-                       f"instructions per link at {SM_COUNT} x {FP32_LANES_PER_SM} lanes x "
-                       f"2.07 GHz")
+        raw[f"n{n}_B{B}"] = {"n": n, "B": B, "t64": timed(rd.RD_ABA_FP64_UPDATE), "tdf": timed(0)}
+    return raw
+
+
+def fd_report(raw, pk):
+    """frac: the kernel's executed FP32 and FP64 arithmetic at the two peaks
+    (combined time) over the measured time; frac_alg: the same with the
+    formulation's count (the method's work: 720 FP32 + 800 FP64 flop per link);
+    df_frac: FP32-pipe issue time of the double-float kernel's instructions."""
+    out = {}
+    for name, r in raw.items():
+        nb = r["n"] * r["B"]
+        t_exec = nb * (FD_EXEC_FLOP32_PER_LINK / pk.f32 + FD_EXEC_FLOP64_PER_LINK / pk.f64)
+        t_alg = nb * (FD_FLOP32_PER_LINK / pk.f32 + FD_FLOP64_PER_LINK / pk.f64)
+        t_df = nb * FD_DF_EXEC_FP32_INST_PER_LINK / pk.i32
+        out[name] = {"us": r["t64"] * 1e6, "value": r["B"] / r["t64"], "frac": t_exec / r["t64"],
+                     "frac_alg": t_alg / r["t64"], "df_us": r["tdf"] * 1e6,
+                     "df_value": r["B"] / r["tdf"], "df_frac": t_df / r["tdf"]}
     return out
 
 
 def crossover_section(torch, rd, chaingen, dev, dist, sampler, K):
     """The inverse-dynamics workload's other sizes: n = 16 and 100 at the same
-    batch (AUTO), and the lane-parallel scan against the serial recursion at
-    n = 32 across small batches."""
-    out = {}
+    batch (AUTO), and AUTO / the serial recursion / the 16-lane scan at n = 32
+    across small batches (4 input sets rotated; small batches stay in L2, as
+    they do in use)."""
+    raw = {}
 
     def case(n, B, variant):
         model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
@@ -423,36 +458,39 @@ def crossover_section(torch, rd, chaingen, dev, dist, sampler, K):
         def call(k):
             rd.rnea(model, *sets[k % len(sets)], out=o, variant=variant)
 
-        t = time_calls(torch, call, steps, 3, dist, sampler)
-        return t / steps, rd.rnea_last_config()
+        return time_calls(torch, call, steps, 3, dist, sampler) / steps
 
     for n in (16, 100):
-        t, fam = case(n, BATCH, rd.RD_VARIANT_AUTO)
-        out[f"n{n}_B{BATCH}"] = {
-            "value": BATCH / t, "unit": UNIT, "ms_per_step": t * 1e3, "kernel_family": fam[0],
-            "stored_links": fam[2],
-            "algorithmic_frac_of_fp32_peak":
-                BATCH * n * ALGO_FLOP_PER_LINK / t / (fp32_peak_tflops() * 1e12)}
+        raw[f"n{n}_B{BATCH}"] = {"n": n, "t": case(n, BATCH, rd.RD_VARIANT_AUTO)}
     for B in (1024, 2048, 4096, 8192):
-        row = {}
-        for name, v in (("auto", rd.RD_VARIANT_AUTO), ("serial", rd.RD_VARIANT_SERIAL_DH),
-                        ("scan16", rd.RD_VARIANT_SCAN(16))):
-            t, fam = case(N_LINKS, B, v)
-            row[name] = t * 1e6
-            if name == "auto":
-                row["auto_kernel_family"] = fam[0]
-        out[f"n{N_LINKS}_B{B}_us"] = row
-    out["metric"] = ("RNEA FP32: evals/s at n = 16 and 100 (B = 65536, AUTO); microseconds per "
-                     "call at n = 32 for small B: AUTO, the serial common-normal recursion and the "
-                     "16-lane scan")
-    out["inputs"] = "4 input sets rotated; the small batches are L2-resident, as they are in use"
+        raw[f"n{N_LINKS}_B{B}_us"] = [case(N_LINKS, B, v) * 1e6 for v in
+                                      (rd.RD_VARIANT_AUTO, rd.RD_VARIANT_SERIAL_DH,
+                                       rd.RD_VARIANT_SCAN(16))]
+    return raw
+
+
+def crossover_report(raw, pk):
+    """n16/n100: algorithmic fraction of the FP32 peak; n32_B*_us: microseconds
+    per call as [AUTO, serial, 16-lane scan]."""
+    out = {}
+    for name, r in raw.items():
+        if isinstance(r, dict):
+            out[name] = {"us": r["t"] * 1e6, "value": BATCH / r["t"],
+                         "frac": BATCH * r["n"] * ALGO_FLOP_PER_LINK / r["t"] / pk.f32}
+        else:
+            out[name] = r
     return out
 
 
-def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
-    from paper_1609_04493_gb300 import autotune
+def uneven_workload(rd, count=100000, seed=None):
+    """The uneven-batch workload: `count` requests, each with its own robot
+    (seed base + k), n uniform in 6..100, 20% forward dynamics, and its joint
+    inputs (FP32; tau ~ N(0, 10) for forward, qdd ~ N(0, 2) for inverse
+    dynamics). Returns (requests, fleet, plan, kinds, [q, qd, in2])."""
+    import chaingen
 
-    reqs = chaingen.uneven_requests(count, n_lo=6, n_hi=100, fd_fraction=0.2, seed=chaingen.BASE_SEED)
+    seed = chaingen.BASE_SEED if seed is None else seed
+    reqs = chaingen.uneven_requests(count, n_lo=6, n_hi=100, fd_fraction=0.2, seed=seed)
     fleet = rd.Fleet([r["chain"] for r in reqs])
     kinds = np.array([1 if r["kind"] == "fd" else 0 for r in reqs], dtype=np.int32)
     plan = rd.Plan(fleet, np.arange(count, dtype=np.int32), kinds, dtype="float32")
@@ -460,47 +498,49 @@ def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
     rng = np.random.default_rng(77)
     fd_mask = np.repeat(kinds, plan.lengths) == 1
     in2 = np.where(fd_mask, rng.normal(0, 10, J), rng.normal(0, 2, J))
-    x = [torch.from_numpy(a.astype(np.float32)).to(dev)
-         for a in (rng.uniform(-np.pi, np.pi, J), rng.normal(0, 1, J), in2)]
+    host = [a.astype(np.float32) for a in (rng.uniform(-np.pi, np.pi, J), rng.normal(0, 1, J), in2)]
+    return reqs, fleet, plan, kinds, host
+
+
+def uneven_section(torch, rd, chaingen, dev, dist, sampler, K, count=100000):
+    from paper_1609_04493_gb300 import autotune
+
+    reqs, fleet, plan, kinds, host = uneven_workload(rd, count)
+    x = [torch.from_numpy(a).to(dev) for a in host]
     o = torch.empty_like(x[0])
     f64 = rd.RD_FLEET_FP64_UPDATE
     (sched, tune), _ = autotune.tune_fleet(plan, *x, out=o, flags=f64)
     (sched_df, tune_df), _ = autotune.tune_fleet(plan, *x, out=o)
     steps = max(3, min(K, 20))
-    res = {}
-    for name, (sc, tu) in (("persistent_tuned", (sched | f64, tune)),
-                           ("per_group_launches", (rd.RD_SCHED_PER_GROUP | f64, 0)),
-                           ("double_float_persistent_tuned", (sched_df, tune_df))):
+    raw = {"count": count, "joints": plan.total_joints, "groups": plan.groups,
+           "fd_joints": int(np.sum(np.where(kinds == 1, plan.lengths, 0)))}
+    for name, (sc, tu) in (("persistent", (sched | f64, tune)),
+                           ("per_group", (rd.RD_SCHED_PER_GROUP | f64, 0)),
+                           ("df_persistent", (sched_df, tune_df))):
         t = time_calls(torch, lambda k: rd.fleet_batch(plan, *x, out=o, schedule=sc, tune=tu),
                        steps, 3, dist, sampler)
-        res[name] = {"value": count * steps / t, "unit": "requests/s",
-                     "ms_per_step": t / steps * 1e3, "steps": steps,
-                     "schedule": sc, "tune": tu}
-    n_fd = int(np.sum(np.where(kinds == 1, plan.lengths, 0)))
-    n_id = J - n_fd
-    t_id = n_id * max(ALGO_FLOP_PER_LINK / (fp32_peak_tflops() * 1e12),
-                      UNEVEN_ID_BYTES_PER_LINK / (measured_peaks().get("hbm_gbs", 6800.0) * 1e9))
-    t_alg = t_id + n_fd * (FD_EXEC_FLOP32_PER_LINK / (fp32_peak_tflops() * 1e12)
-                           + FD_EXEC_FLOP64_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12))
-    t_alg_df = t_id + n_fd * FD_DF_EXEC_FP32_INST_PER_LINK / (SM_COUNT * FP32_LANES_PER_SM * 2.070e9)
-    for name in ("persistent_tuned", "per_group_launches"):
-        res[name]["roofline_frac"] = t_alg / (res[name]["ms_per_step"] * 1e-3)
-    res["double_float_persistent_tuned"]["roofline_frac"] = t_alg_df / (
-        res["double_float_persistent_tuned"]["ms_per_step"] * 1e-3)
-    res["roofline_ms"] = t_alg * 1e3
-    res["roofline"] = (f"inverse dynamics links at the larger of {ALGO_FLOP_PER_LINK} flop / FP32 "
-                       f"peak and {UNEVEN_ID_BYTES_PER_LINK} B (joint values, torque, streamed "
-                       f"constants) / measured HBM bandwidth, plus forward dynamics links at the "
-                       f"combined FP32 + FP64 time of {FD_EXEC_FLOP32_PER_LINK} FP32 and "
-                       f"{FD_EXEC_FLOP64_PER_LINK} FP64 flop per link (double-float line: the "
-                       f"FP32-pipe issue time of {FD_DF_EXEC_FP32_INST_PER_LINK} instructions "
-                       f"per link); divided by the measured time")
-    res["workload"] = (f"{count} requests, own robot each, n uniform in 6..100 "
-                       f"({J} joints), {int(kinds.sum())} forward / {count - int(kinds.sum())} "
-                       f"inverse dynamics, FP32 with FP64 inertia updates and solves (the "
-                       f"double-float line: the library's default)")
-    res["launches_per_group_schedule"] = plan.groups
-    return res
+        raw[name] = {"t": t / steps, "schedule": sc, "tune": tu}
+    return raw
+
+
+def uneven_report(raw, pk):
+    """frac: inverse-dynamics links at the larger of their FP32 time (470 flop)
+    and HBM time (128 B), plus forward-dynamics links at the combined time of
+    the kernel's executed FP32 + FP64 flop (df: FP32-pipe issue time of the
+    double-float instructions), over the measured time."""
+    n_fd = raw["fd_joints"]
+    n_id = raw["joints"] - n_fd
+    t_id = n_id * max(ALGO_FLOP_PER_LINK / pk.f32, UNEVEN_ID_BYTES_PER_LINK / pk.hbm)
+    t_fd = n_fd * (FD_EXEC_FLOP32_PER_LINK / pk.f32 + FD_EXEC_FLOP64_PER_LINK / pk.f64)
+    t_df = n_fd * FD_DF_EXEC_FP32_INST_PER_LINK / pk.i32
+    out = {}
+    for name in ("persistent", "per_group", "df_persistent"):
+        r = raw[name]
+        floor = t_id + (t_df if name == "df_persistent" else t_fd)
+        out[name] = {"us": r["t"] * 1e6, "value": raw["count"] / r["t"], "frac": floor / r["t"],
+                     "sched": r["schedule"], "tune": r["tune"]}
+    out["launches_per_group"] = raw["groups"]
+    return out
 
 
 def timed_graph(torch, g, dist, sampler):
@@ -531,6 +571,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     rd.load()
     props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
     uuid = getattr(props, "uuid", None)
     sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else None) if rank == 0 else None
 
@@ -546,11 +587,69 @@ def run_ours(args):
     g32 = capture(torch, rd, model, sets32, K)
     t32 = max_over_ranks(dist, timed_graph(torch, g32, dist, sampler))
     value = world * BATCH * K / t32
-    ms_step = t32 / K * 1e3
+    kern_id, kern_block, kern_stored = rd.rnea_last_config()
+    del g32, gw
+
+    raw = {}
+    if not args.quick:
+        # ---- FP64 on the same GPU, IEEE FP64 and double-float arithmetic
+        K64 = max(3, min(K, 200))
+        sets64 = make_inputs(torch, dev, torch.float64, 4, 2000 + 100 * rank)
+        t64 = {}
+        for name, v in (("fp64", rd.RD_VARIANT_AUTO), ("df", rd.RD_VARIANT_SERIAL_DF)):
+            gw64 = capture(torch, rd, model, sets64, 3, variant=v)
+            gw64.replay()
+            torch.cuda.synchronize()
+            g64 = capture(torch, rd, model, sets64, K64, variant=v)
+            t64[name] = max_over_ranks(dist, timed_graph(torch, g64, dist, sampler)) / K64
+            del g64, gw64
+        x0 = sets64[0]
+        ref64 = rd.rnea(model, x0["q"], x0["qd"], x0["qdd"])
+        got = rd.rnea(model, x0["q"], x0["qd"], x0["qdd"], variant=rd.RD_VARIANT_SERIAL_DF)
+        scale = ref64.abs().amax(dim=1).clamp_min(1e-300)
+        t64["df_diff"] = float(((got - ref64).abs().amax(dim=1) / scale).max())
+        raw["fp64"] = t64
+        del sets64
+
+        # ---- end to end through the host-array entry point: two sets of
+        # pinned host inputs alternate, so no step reads the previous one's
+        hosts = []
+        for r in range(2):
+            st = chaingen.make_states(BATCH, N_LINKS, seed=3000 + 10 * rank + r)
+            hosts.append(([torch.from_numpy(st[k].astype(np.float32)).pin_memory()
+                           for k in ("q", "qd", "qdd")],
+                          torch.empty((BATCH, N_LINKS), dtype=torch.float32).pin_memory()))
+        Ke = max(4, min(K, 200))
+        e2e = {}
+        for name, v in (("inplace", rd.RD_VARIANT_AUTO), ("staged", rd.RD_FLAG_HOST_COPY)):
+            for k in range(3):
+                rd.rnea_host(model, *hosts[k % 2][0], out=hosts[k % 2][1], variant=v)
+            barrier(dist)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(Ke):
+                rd.rnea_host(model, *hosts[k % 2][0], out=hosts[k % 2][1], variant=v)
+            te = max_over_ranks(dist, time.perf_counter() - t0)
+            barrier(dist)
+            if sampler is not None:
+                sampler.region(t0, t0 + te)
+            e2e[name] = te / Ke
+        raw["e2e"] = e2e
+        raw["e2e_steps"] = Ke
+
+        raw["adjoint"] = adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K)
+        raw["forward_dynamics"] = fd_section(torch, rd, chaingen, dev, dist, sampler, K)
+        raw["crossover"] = crossover_section(torch, rd, chaingen, dev, dist, sampler, K)
+        if not args.no_uneven:
+            raw["uneven"] = uneven_section(torch, rd, chaingen, dev, dist, sampler, K)
+
+    clocks = sampler.stop() if sampler is not None else None
+    mhz = (clocks or {}).get("sm_mhz") or SM_MAX_MHZ
+    pk = Peaks(sm_count, mhz)
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-           "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "warmup": W, "ms_per_step": t32 / K * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n_links": N_LINKS, "batch": BATCH,
                       "global_batch": BATCH * world, "parallelism": f"replicas{world}",
                       "l2": f"{ROTATE} rotating input sets "
@@ -558,145 +657,57 @@ def run_ours(args):
                       "seed": chaingen.BASE_SEED},
            "gpu_launches": K}
 
-    # roofline of the dominant kernel (the FP32 RNEA kernel: one launch per step)
-    kern_id, kern_block, kern_stored = rd.rnea_last_config()
+    # roofline of the dominant kernel (one FP32 RNEA launch per step)
     if kern_id == rd.RD_RNEA_KERNEL_DH_PARAM:
-        kname = (f"rnea_dhp_kernel<float, {kern_block} threads>, common-normal frames, "
-                 f"constants as a kernel parameter, full state for {kern_stored} of "
-                 f"{N_LINKS} links, polynomial sin/cos")
+        kname = f"rnea_dhp_kernel<float,{kern_block}>,K={kern_stored}"
         exec_fpl = dh_param_flops(N_LINKS, kern_stored) / N_LINKS
     else:
-        kname = f"rnea kernel family {kern_id:#x}, {kern_block} threads"
+        kname = f"rnea family {kern_id:#x},{kern_block}"
         exec_fpl = JOINT_FRAME_FLOP_PER_LINK
     avg_launch = t32 / K
-    peak32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
     achieved = ALGO_FLOP_PER_LINK * N_LINKS * BATCH / avg_launch / 1e12
     executed = exec_fpl * N_LINKS * BATCH / avg_launch / 1e12
-    traffic = recorded_traffic("rnea_fp32_n32_B65536")
-    try:
-        fma32 = rd.measure_fma_peak("float32")
-        fma64 = rd.measure_fma_peak("float64")
-    except Exception:  # diagnostic only
-        fma32 = fma64 = None
-    res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                       "frac": achieved / peak32, "traffic": traffic,
+    peak = pk.f32 / 1e12
+    res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak,
+                       "traffic": recorded_traffic("rnea_fp32_n32_B65536"),
                        "kernel": kname, "avg_launch_us": avg_launch * 1e6,
                        "flop_per_link": ALGO_FLOP_PER_LINK,
-                       "flop_count": "algorithmic: the recursion of Sec. II-A with general link "
-                                     "transforms (Rodrigues exponential and 3x4 compose), FMA = 2",
-                       "executed_flop_per_link": exec_fpl,
-                       "executed_tflops": executed, "executed_frac": executed / peak32,
-                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                       "measured_fma_tflops": {"fp32": fma32, "fp64": fma64},
-                       "hbm": {"algorithmic_bytes_per_launch": BATCH * N_LINKS * 16,
-                               "achieved_gbs": BATCH * N_LINKS * 16 / avg_launch / 1e9,
-                               "peak_gbs": measured_peaks().get("hbm_gbs", 6800.0),
-                               "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}
-
-    if not args.quick:
-        # ---- FP64 on the same GPU
-        K64 = max(3, min(K, 200))
-        del g32, gw
-        sets64 = make_inputs(torch, dev, torch.float64, 4, 2000 + 100 * rank)
-        gw64 = capture(torch, rd, model, sets64, 3)
-        gw64.replay()
-        torch.cuda.synchronize()
-        g64 = capture(torch, rd, model, sets64, K64)
-        t64 = max_over_ranks(dist, timed_graph(torch, g64, dist, sampler))
-        k64 = rd.rnea_last_config()
-        fp64_flops = ALGO_FLOP_PER_LINK * N_LINKS * BATCH / (t64 / K64) / 1e12
-        fp64_exec = JOINT_FRAME_FLOP_PER_LINK * N_LINKS * BATCH / (t64 / K64) / 1e12
-        res["fp64"] = {"value": world * BATCH * K64 / t64, "unit": UNIT, "steps": K64,
-                       "ms_per_step": t64 / K64 * 1e3, "kernel_family": k64[0],
-                       "flop_per_link": JOINT_FRAME_FLOP_PER_LINK,
-                       "achieved_tflops": fp64_exec, "peak_tflops_nominal": FP64_NOMINAL_TFLOPS,
-                       "frac_of_nominal": fp64_exec / FP64_NOMINAL_TFLOPS,
-                       "frac_of_measured_fma": (fp64_exec / fma64) if fma64 else None,
-                       "algorithmic_tflops": fp64_flops,
-                       "algorithmic_frac_of_nominal": fp64_flops / FP64_NOMINAL_TFLOPS,
-                       "fp32_over_fp64": value / (world * BATCH * K64 / t64)}
-        # the same FP64 data in double-float arithmetic on the FP32 pipe
-        vdf = rd.RD_VARIANT_SERIAL_DF
-        gwdf = capture(torch, rd, model, sets64, 3, variant=vdf)
-        gwdf.replay()
-        torch.cuda.synchronize()
-        gdf = capture(torch, rd, model, sets64, K64, variant=vdf)
-        tdf = max_over_ranks(dist, timed_graph(torch, gdf, dist, sampler))
-        x0 = sets64[0]
-        ref64 = rd.rnea(model, x0["q"], x0["qd"], x0["qdd"])
-        got = rd.rnea(model, x0["q"], x0["qd"], x0["qdd"], variant=vdf)
-        scale = ref64.abs().amax(dim=1).clamp_min(1e-300)
-        diff = float(((got - ref64).abs().amax(dim=1) / scale).max())
-        t_issue = N_LINKS * BATCH * RNEA_DF_EXEC_FP32_INST_PER_LINK / (
-            SM_COUNT * FP32_LANES_PER_SM * 2.070e9)
-        t_floor = N_LINKS * BATCH * JOINT_FRAME_FLOP_PER_LINK / (FP64_NOMINAL_TFLOPS * 1e12)
-        res["fp64"]["double_float"] = {
-            "value": world * BATCH * K64 / tdf, "unit": UNIT, "steps": K64,
-            "ms_per_step": tdf / K64 * 1e3, "variant": "RD_VARIANT_SERIAL_DF",
-            "fp32_inst_per_link": RNEA_DF_EXEC_FP32_INST_PER_LINK,
-            "roofline_ms": t_issue * 1e3, "roofline_frac": t_issue / (tdf / K64),
-            "fp64_pipe_floor_ms": t_floor * 1e3,
-            "max_rel_diff_vs_fp64": diff,
-            "roofline": ("FP32-pipe issue time of the kernel's FP32 instructions per link at "
-                         f"{SM_COUNT} x {FP32_LANES_PER_SM} lanes x 2.07 GHz over the measured "
-                         "time; fp64_pipe_floor_ms: the FP64 kernel's executed "
-                         f"{JOINT_FRAME_FLOP_PER_LINK} flop per link at the nominal FP64 peak")}
-        del g64, gw64, gdf, gwdf, sets64
-
-        # ---- end to end through the host-array entry point
-        st = chaingen.make_states(BATCH, N_LINKS, seed=3000 + rank)
-        host = [torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("q", "qd", "qdd")]
-        out = torch.empty_like(host[0]).pin_memory()
-        for _ in range(3):
-            rd.rnea_host(model, *host, out=out)
-        Ke = max(3, min(K, 200))
-        barrier(dist)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(Ke):
-            rd.rnea_host(model, *host, out=out)
-        te = max_over_ranks(dist, time.perf_counter() - t0)
-        barrier(dist)
-        if sampler is not None:
-            sampler.region(t0, t0 + te)
-        res["e2e"] = {"value": world * BATCH * Ke / te, "unit": UNIT, "steps": Ke,
-                      "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
-                      "d2h_bytes_per_step": BATCH * N_LINKS * 4,
-                      "api": "rnea_batch_host, pinned host arrays, FP32: the kernel reads "
-                             "the rows from host memory and writes tau back itself (16-byte "
-                             "slab transfers; RD_RNEA_KERNEL_DH_HOST)"}
-        # the staged path on the same arrays: copy engines, row chunks pipelined
-        # over three streams
-        for _ in range(3):
-            rd.rnea_host(model, *host, out=out, variant=rd.RD_FLAG_HOST_COPY)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(Ke):
-            rd.rnea_host(model, *host, out=out, variant=rd.RD_FLAG_HOST_COPY)
-        ts = max_over_ranks(dist, time.perf_counter() - t0)
-        res["e2e"]["staged_copies"] = {"value": world * BATCH * Ke / ts, "unit": UNIT,
-                                       "ms_per_step": ts / Ke * 1e3}
-        link_bytes = 4 * BATCH * N_LINKS * 4
-        res["e2e"]["link_gbs"] = link_bytes / (te / Ke) / 1e9
-
-        # ---- adjoint (rnea_vjp), n = 32 FP32
-        res["adjoint"] = adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K)
-        # ---- forward dynamics (aba_batch), n = 16 and 64, B = 16384 FP32
-        res["forward_dynamics"] = fd_section(torch, rd, chaingen, dev, dist, sampler, K)
-        # ---- the inverse-dynamics workload's other sizes and the scan / serial crossover
-        res["crossover"] = crossover_section(torch, rd, chaingen, dev, dist, sampler, K)
-        # ---- uneven batching: 100000 mixed requests (fleet_batch)
-        if not args.no_uneven:
-            res["uneven"] = uneven_section(torch, rd, chaingen, dev, dist, sampler, K)
-
-    if sampler is not None:
-        res["clocks"] = sampler.stop()
+                       "executed_flop_per_link": exec_fpl, "executed_frac": executed / peak,
+                       "peak_src": f"{sm_count}SMx128x2x{mhz:.0f}MHz",
+                       "hbm_frac": BATCH * N_LINKS * 16 / avg_launch / pk.hbm}
+    if clocks is not None:
+        res["clocks"] = {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(target_s=10.0)
+    if "e2e" in raw:
+        te, Ke = raw["e2e"], raw["e2e_steps"]
+        res["e2e"] = {"value": world * BATCH / te["inplace"], "unit": UNIT, "steps": Ke,
+                      "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
+                      "d2h_bytes_per_step": BATCH * N_LINKS * 4,
+                      "api": "rnea_batch_host", "host_sets": 2,
+                      "link_gbs": 4 * BATCH * N_LINKS * 4 / te["inplace"] / 1e9,
+                      "staged_value": world * BATCH / te["staged"]}
+    if "crossover" in raw:
+        res["crossover"] = crossover_report(raw["crossover"], pk)
+    if "uneven" in raw:
+        res["uneven"] = uneven_report(raw["uneven"], pk)
+    if "fp64" in raw:
+        t = raw["fp64"]
+        nb = N_LINKS * BATCH
+        res["fp64"] = {"us": t["fp64"] * 1e6, "value": world * BATCH / t["fp64"],
+                       "frac": nb * JOINT_FRAME_FLOP_PER_LINK / t["fp64"] / pk.f64,
+                       "df_us": t["df"] * 1e6, "df_value": world * BATCH / t["df"],
+                       "df_frac": nb * RNEA_DF_EXEC_FP32_INST_PER_LINK / pk.i32 / t["df"],
+                       "df_diff": t["df_diff"]}
+    if "forward_dynamics" in raw:
+        res["forward_dynamics"] = fd_report(raw["forward_dynamics"], pk)
+    if "adjoint" in raw:
+        res["adjoint"] = adjoint_report(raw["adjoint"], pk)
     if dist is not None:
         dist.destroy_process_group()
     if rank == 0:
-        print(json.dumps(res), flush=True)
+        print(json.dumps(rnd(res)), flush=True)
 
 
 # -------------------------------------------------------- CPU (oracle) arm
@@ -710,24 +721,23 @@ def _cpu_threads():
 
 def cpu_baseline(target_s=10.0, threads=None):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of the
-    headline workload (same chain, fresh states), batch split over threads."""
+    headline workload (same chain, fresh states, the batch split over
+    threads), evaluated in passes until about `target_s` seconds of work."""
     import chaingen
     import oracle
 
     threads = threads or _cpu_threads()
     chain = chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED)
-    probe = chaingen.make_states(256 * threads, N_LINKS, seed=4242)
-    t0 = time.perf_counter()
-    oracle.rnea_threaded(chain, probe["q"], probe["qd"], probe["qdd"], threads=threads)
-    rate = 256 * threads / max(time.perf_counter() - t0, 1e-6)
-    sample = int(min(max(rate * target_s / threads, 1024), 4 * BATCH))
-    st = chaingen.make_states(sample, N_LINKS, seed=4343)
-    t0 = time.perf_counter()
-    oracle.rnea_threaded(chain, st["q"], st["qd"], st["qdd"], threads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{sample} states of the n=32 chain (FP64 oracle, {threads} threads, "
-                      f"{dt:.1f} s)"}
+    st = chaingen.make_states(BATCH, N_LINKS, seed=4343)
+    passes, t0 = 0, time.perf_counter()
+    while True:
+        oracle.rnea_threaded(chain, st["q"], st["qd"], st["qdd"], threads=threads)
+        passes += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return {"value": passes * BATCH / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{passes}x{BATCH} states n=32, FP64 oracle, {threads} threads, {dt:.1f} s"}
 
 
 def run_reference(args):

@@ -11,10 +11,36 @@ if ROOT not in sys.path:
 import bench  # noqa: E402
 
 
-def test_fp32_peak_is_lanes_times_clock():
+def test_peaks_scale_with_sm_count_and_clock():
     # 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.070 GHz
     assert abs(bench.fp32_peak_tflops() - 152 * 128 * 2 * 2.070e9 / 1e12) < 1e-9
     assert abs(bench.fp32_peak_tflops() - 80.548) < 1e-3
+    # FP64: 2 FMAs per SM per clock, 1.26 TFLOP/s at 152 SMs and 2.07 GHz
+    assert abs(bench.fp64_peak_tflops() - 1.2586) < 1e-4
+    assert abs(bench.fp32_peak_tflops(148, 1800.0) - 148 * 128 * 2 * 1.8e9 / 1e12) < 1e-9
+    assert abs(bench.fp64_peak_tflops(76, 1000.0) / bench.fp64_peak_tflops(152, 2000.0) - 0.25) < 1e-12
+    assert bench.fp32_inst_rate(152, 2070.0) == 152 * 128 * 2070.0e6
+
+
+def test_fractions_are_work_over_time_at_the_sampled_clock():
+    pk = bench.Peaks(152, 1035.0)  # half the maximum clock: half the peak
+    assert abs(pk.f32 - bench.fp32_peak_tflops() * 1e12 / 2) < 1.0
+    t = 1e-5
+    adj = bench.adjoint_report({"B8192_recompute": {"B": 8192, "mode": 2, "t": t}}, pk)
+    r = adj["B8192_recompute"]
+    assert abs(r["frac"] - 8192 * 32 * 772 / t / pk.f32) < 1e-12
+    assert r["frac"] < 1.0 or t < 8192 * 32 * 772 / pk.f32
+    fd = bench.fd_report({"n64_B16384": {"n": 64, "B": 16384, "t64": 6e-4, "tdf": 3e-4}}, pk)
+    f = fd["n64_B16384"]
+    nb = 64 * 16384
+    assert abs(f["frac"] - nb * (257 / pk.f32 + 400 / pk.f64) / 6e-4) < 1e-12
+    assert abs(f["frac_alg"] - nb * (720 / pk.f32 + 800 / pk.f64) / 6e-4) < 1e-12
+    assert abs(f["df_frac"] - nb * 3043 / pk.i32 / 3e-4) < 1e-12
+
+
+def test_rounding_keeps_four_significant_digits():
+    x = bench.rnd({"a": 2806440547.738912, "b": [0.5240223181402908, 3], "c": "s", "d": None})
+    assert x == {"a": 2806000000.0, "b": [0.524, 3], "c": "s", "d": None}
 
 
 def test_executed_flops_follow_the_per_link_parts():

@@ -139,3 +139,53 @@ def test_fleet_fp64_update_flag(cuda_lib, schedule):
     fd = ~id_mask
     scale = np.max(np.abs(ref[fd]))
     assert np.max(np.abs(out[fd] - ref[fd])) <= 1e-4 * scale
+
+
+def _stratified(kinds, lengths, per_group, seed=0):
+    """Up to `per_group` requests of every (kind, n) pair, drawn at random."""
+    rng = np.random.default_rng(seed)
+    pick = []
+    for kind in (0, 1):
+        for n in np.unique(lengths):
+            idx = np.flatnonzero((kinds == kind) & (lengths == n))
+            if len(idx):
+                pick.extend(rng.choice(idx, size=min(per_group, len(idx)), replace=False))
+    return np.sort(np.array(pick))
+
+
+def test_fleet_uneven_workload_at_full_size(cuda_lib):
+    """The bench's uneven workload exactly (100000 requests from seed 1609,
+    its inputs, FP32): the persistent launch with FP64 inertia updates and
+    solves, one launch per (kind, n) group with the same, and the persistent
+    launch with the double-float default. 11 requests of every (kind, n) pair,
+    n = 6..100 (2090 requests), checked against the oracle on the FP32 bars."""
+    import torch
+
+    import bench
+
+    rd = cuda_lib
+    reqs, fleet, plan, kinds, host = bench.uneven_workload(rd, 100000)
+    lengths = np.asarray(plan.lengths)
+    assert set(np.unique(lengths)) == set(range(6, 101))
+    sample = _stratified(kinds, lengths, 11, seed=1)
+    assert len(sample) >= 2000
+    assert {int(n) for n in lengths[sample[kinds[sample] == 1]]} == set(range(6, 101))
+    assert {int(n) for n in lengths[sample[kinds[sample] == 0]]} == set(range(6, 101))
+    x = [torch.from_numpy(a).cuda() for a in host]
+    h64 = [a.astype(np.float64) for a in host]
+    refs = {}
+    for r in sample:
+        o, n = plan.offsets[r], plan.lengths[r]
+        sl = slice(o, o + n)
+        fn = oracle.rnea if kinds[r] == 0 else oracle.fd_aba
+        refs[r] = fn(reqs[r]["chain"], h64[0][sl][None], h64[1][sl][None], h64[2][sl][None])
+    f64 = rd.RD_FLEET_FP64_UPDATE
+    for schedule in (0 | f64, rd.RD_SCHED_PER_GROUP | f64, 0):
+        out = rd.fleet_batch(plan, *x, schedule=schedule).cpu().numpy().astype(np.float64)
+        worst = {0: 0.0, 1: 0.0}
+        for r in sample:
+            o, n = plan.offsets[r], plan.lengths[r]
+            e = oracle.rel_err(out[o:o + n][None], refs[r])
+            worst[int(kinds[r])] = max(worst[int(kinds[r])], e)
+        assert worst[0] <= TOL_ID["float32"], (schedule, worst)
+        assert worst[1] <= TOL_FD["float32"], (schedule, worst)
