@@ -268,12 +268,11 @@ int rnea_vjp_workspace_size(const rd_model *model, int B, int dtype, size_t *byt
 #define RD_VJP_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /*
- * rnea_vjp_noalloc -- rnea_vjp (the adjoint of the recursions of Sec. II-A) in
- * RD_VJP_STORE mode for callers that cannot allocate device memory when they
- * call (a real-time loop with a no-allocation rule, a plug-in whose host
- * framework owns the memory pool).
- * This is an interface convenience of the library; the paper has no
- * counterpart.
+ * rnea_vjp_noalloc -- rnea_vjp in RD_VJP_STORE mode with library-owned
+ * scratch, for callers that cannot allocate device memory when they call (a
+ * real-time loop with a no-allocation rule, a plug-in whose host framework
+ * owns the memory pool). The paper has no counterpart: this is an interface
+ * convenience of the library.
  *
  * The caller passes inputs and outputs exactly as for rnea_vjp. The store-mode
  * scratch comes from a file-scope device array of RD_VJP_NOALLOC_SCRATCH_BYTES
@@ -285,7 +284,8 @@ int rnea_vjp_workspace_size(const rd_model *model, int B, int dtype, size_t *byt
  *     B <= 13107).
  *   - Set-up: the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture. The address is kept for the life of the
+ *     process: do not call cudaDeviceReset while the library is in use.
  *   - Sharing: all calls share the one array and it keeps the last call's
  *     contents; every slot is written before it is read, so nothing is cleared.
  *     Calls that overlap on the GPU (other streams, other threads) race on it:

@@ -28,7 +28,8 @@ std::mutex g_scratch_mu;
 void *g_scratch_ptr[64] = {};
 
 // Device address of the scratch array on the current device (looked up on the
-// first call per device).
+// first call per device and kept for the life of the process; a
+// cudaDeviceReset while the library is in use would leave it stale).
 int scratch_address(int device, void **out)
 {
     if (device < 0 || device >= 64)
