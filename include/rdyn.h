@@ -70,6 +70,19 @@ enum rd_status {
  * instead, in the same frames. Ignored for RD_F64. */
 #define RD_ABA_FP64_UPDATE 0x4
 
+/* aba_batch flags, RD_F32 only: the precision of the bias sweeps (the motion and
+ * bias wrenches of tau_bias = ID(q, qd, 0, ...), the wrench carry, tau_hat and
+ * the joint sin/cos). Along a long chain under gravity the bias torques grow
+ * far above tau, and their FP32 rounding, amplified by the conditioning of
+ * M(q), sets the error of qdd (n = 128: 2e-3 of max|qdd|). By default chains
+ * longer than RD_ABA_EXTENDED_BIAS_LINKS run these sweeps in double-float
+ * arithmetic (about 48 bits, on the FP32 pipe), shorter ones in FP32.
+ * RD_ABA_EXTENDED_BIAS asks for double-float at any n, RD_ABA_FP32_BIAS for
+ * FP32 at any n (comparisons). Ignored for RD_F64, whose sweeps run in FP64. */
+#define RD_ABA_EXTENDED_BIAS 0x8
+#define RD_ABA_FP32_BIAS 0x10
+#define RD_ABA_EXTENDED_BIAS_LINKS 64
+
 /* Per-instance status word of aba_batch (0 = fine). */
 #define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */
 
@@ -304,7 +317,9 @@ int rnea_vjp_noalloc(const rd_model *model, int B, int dtype, const void *q, con
  * recursions of Eq. recursive-fd (the scans of Sec. III-D; Algorithm 3 without
  * its CPU stage). Arithmetic in dtype, except the articulated-inertia update
  * and the divisions by Omega_i = S_i^T J_hat_i S_i: FP64 for RD_F64 data (and
- * with RD_ABA_FP64_UPDATE); double-float (about 48 bits) for RD_F32 data.
+ * with RD_ABA_FP64_UPDATE); double-float (about 48 bits) for RD_F32 data. For
+ * RD_F32 data the bias sweeps run in double-float for n >
+ * RD_ABA_EXTENDED_BIAS_LINKS (see RD_ABA_EXTENDED_BIAS).
  *
  *   q, qd, tau  device, [B, n] row-major inputs; qdd device [B, n] output.
  *   base        as in rnea_batch.

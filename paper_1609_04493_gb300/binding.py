@@ -407,6 +407,9 @@ def rnea_autograd(model, q, qd, qdd, base=None, vjp_mode=RD_VJP_RECOMPUTE):
 RD_ABA_SCANS_IN_DTYPE = 0x1
 RD_ABA_JOINT_FRAMES = 0x2
 RD_ABA_FP64_UPDATE = 0x4
+RD_ABA_EXTENDED_BIAS = 0x8
+RD_ABA_FP32_BIAS = 0x10
+RD_ABA_EXTENDED_BIAS_LINKS = 64
 
 
 def aba_workspace_bytes(model, B, dtype_code, flags=0):

@@ -30,6 +30,7 @@
 
 #include "aba.cuh"
 #include "df.cuh"
+#include "df_trig.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
@@ -163,6 +164,40 @@ __device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, con
     return o;
 }
 
+// Sweep-1 state of a link, F_hat (6) then cos, sin, in the bias precision TB:
+// for TB = T the slots 0..5, 8, 9 of the kAbaStateScalars-wide layout; for TB
+// = DF eight pairs per link, [link][8][instance], in the same workspace
+// (aba_bias_ws_scalars floats per link and instance).
+constexpr int kAbaBiasPairs = 8;
+
+template <typename T, typename TB>
+__host__ __device__ constexpr int aba_bias_ws_scalars()
+{
+    return std::is_same<TB, T>::value ? kAbaStateScalars : 2 * kAbaBiasPairs;
+}
+
+template <typename TB, typename T>
+__device__ __forceinline__ void bias_put(T *ws, int B, int b, int i, int k, TB v)
+{
+    if constexpr (std::is_same<TB, T>::value) {
+        aba_put(ws, B, b, i, k < 6 ? k : k + 2, v);
+    } else {
+        TB *w = reinterpret_cast<TB *>(ws);
+        w[((size_t)i * kAbaBiasPairs + k) * (size_t)B + b] = v;
+    }
+}
+
+template <typename TB, typename T>
+__device__ __forceinline__ TB bias_get(const T *ws, int B, int b, int i, int k)
+{
+    if constexpr (std::is_same<TB, T>::value) {
+        return aba_get(ws, B, b, i, k < 6 ? k : k + 2);
+    } else {
+        const TB *w = reinterpret_cast<const TB *>(ws);
+        return w[((size_t)i * kAbaBiasPairs + k) * (size_t)B + b];
+    }
+}
+
 // One forward-dynamics instance in common-normal frames. sc: the chain's 16
 // constants per link in T; sd: its records in D (FP64, or split into
 // double-float pairs); qr, qdr, taur, qddr: its joint rows (VEC: n % 4 == 0 and
@@ -170,23 +205,32 @@ __device__ __forceinline__ AbiT<D> aba_dh_update(const AbiT<D> &P, D c, D s, con
 // (aba_put; Z is the type of the solve state and of the z_hat / lambda
 // recursions: D, or T). PF: constants, records and workspace live in global
 // memory (fleets), and each sweep prefetches the next link's into L1 while it
-// computes the current one. Returns 1 when an Omega_i <= 0 or a non-finite qdd
-// appeared.
-template <typename T, typename D, typename Z, int TRIG, bool VEC, bool PF = false>
+// computes the current one. TB: precision of the bias sweeps (the motion and
+// bias wrenches of sweep 1, the wrench carry and tau_hat of sweep 2) and of the
+// joint sin/cos: T, or DF for long chains, whose bias torques grow far above
+// tau so that FP32 rounding there sets the error of qdd; with TB = DF they run
+// on sdf, the chain's records as double-float pairs, with the sin/cos of
+// df_trig.cuh. Returns 1 when an Omega_i <= 0 or a non-finite qdd appeared.
+template <typename T, typename D, typename Z, int TRIG, bool VEC, bool PF = false,
+          typename TB = T>
 __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
                                                const T *__restrict__ qr, const T *__restrict__ qdr,
                                                const T *__restrict__ taur, T *__restrict__ qddr,
                                                T *__restrict__ ws, Z *__restrict__ wsz, int B, int b,
-                                               const BaseParams<T> &base)
+                                               const BaseParams<T> &base,
+                                               const DF *__restrict__ sdf = nullptr)
 {
+    constexpr bool kExt = !std::is_same<TB, T>::value;
+    static_assert(!kExt || (std::is_same<TB, DF>::value && sizeof(T) == 4),
+                  "extended bias sweeps: double-float, FP32 data");
     int bad = 0;
 
     // ---- sweep 1: bias motion (qdd = 0) and bias wrenches
-    Motion<T> x;
-    x.v = mk3(base.V0[0], base.V0[1], base.V0[2]);
-    x.w = mk3(base.V0[3], base.V0[4], base.V0[5]);
-    x.a = mk3(base.dV0[0], base.dV0[1], base.dV0[2]);
-    x.al = mk3(base.dV0[3], base.dV0[4], base.dV0[5]);
+    Motion<TB> x;
+    x.v = mk3(dcvt<TB>(base.V0[0]), dcvt<TB>(base.V0[1]), dcvt<TB>(base.V0[2]));
+    x.w = mk3(dcvt<TB>(base.V0[3]), dcvt<TB>(base.V0[4]), dcvt<TB>(base.V0[5]));
+    x.a = mk3(dcvt<TB>(base.dV0[0]), dcvt<TB>(base.dV0[1]), dcvt<TB>(base.dV0[2]));
+    x.al = mk3(dcvt<TB>(base.dV0[3]), dcvt<TB>(base.dV0[4]), dcvt<TB>(base.dV0[5]));
     const int nchunks = (n + 3) / 4;
     for (int kc = 0; kc < nchunks; ++kc) {
         const int i0 = 4 * kc;
@@ -195,18 +239,29 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
         for (int j = 0; j < 4; ++j) {
             const int i = i0 + j;
             if (VEC || i < n) {
-                if (PF && i + 1 < n) prefetch_l1(sc + (i + 1) * kDhConsts);
-                DhLink<T> L;
-                load_dh(sc + i * kDhConsts, L);
-                T s, c;
-                dh_trig<T, TRIG>(cq.v[j] + L.th0, &s, &c);
-                x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, cqd.v[j], T(0), x);
-                const Wrench<T> Fh = bias_wrench(L.m, L.c, L.I, x);
-                const T vals[6] = {Fh.f.x, Fh.f.y, Fh.f.z, Fh.n.x, Fh.n.y, Fh.n.z};
+                TB s, c;
+                Wrench<TB> Fh;
+                if constexpr (kExt) {
+                    const DF *r = sdf + i * kAbaDh64;
+                    if (PF && i + 1 < n) {
+                        prefetch_l1(r + kAbaDh64);
+                        prefetch_l1(r + kAbaDh64 + kAbaDh64 / 2);
+                    }
+                    df_sincos((double)cq.v[j] + df_to_double(r[5]), &s, &c);
+                    x = dh_forward(dh_rot(r[0], r[1], c, s), mk3(r[2], r[3], r[4]),
+                                   DF(cqd.v[j]), DF(0.0f), x);
+                    Fh = bias_wrench(r[6], mk3(r[7], r[8], r[9]), r + 10, x);
+                } else {
+                    if (PF && i + 1 < n) prefetch_l1(sc + (i + 1) * kDhConsts);
+                    DhLink<T> L;
+                    load_dh(sc + i * kDhConsts, L);
+                    dh_trig<T, TRIG>(cq.v[j] + L.th0, &s, &c);
+                    x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, cqd.v[j], T(0), x);
+                    Fh = bias_wrench(L.m, L.c, L.I, x);
+                }
+                const TB vals[8] = {Fh.f.x, Fh.f.y, Fh.f.z, Fh.n.x, Fh.n.y, Fh.n.z, c, s};
 #pragma unroll
-                for (int k = 0; k < 6; ++k) aba_put(ws, B, b, i, k, vals[k]);
-                aba_put(ws, B, b, i, 8, c);
-                aba_put(ws, B, b, i, 9, s);
+                for (int k = 0; k < 8; ++k) bias_put<TB>(ws, B, b, i, k, vals[k]);
             }
         }
     }
@@ -219,15 +274,15 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
     // at one warp per scheduler every miss stalls issue. Its sweeps run one
     // link per iteration.
     constexpr bool kRolled = std::is_same<D, DF>::value;
-    Wrench<T> F;
-    F.f = mk3(base.Fn[0], base.Fn[1], base.Fn[2]);
-    F.n = mk3(base.Fn[3], base.Fn[4], base.Fn[5]);
+    Wrench<TB> F;
+    F.f = mk3(dcvt<TB>(base.Fn[0]), dcvt<TB>(base.Fn[1]), dcvt<TB>(base.Fn[2]));
+    F.n = mk3(dcvt<TB>(base.Fn[3]), dcvt<TB>(base.Fn[4]), dcvt<TB>(base.Fn[5]));
     Wrench<Z> z;
     z.f = z.n = mk3(Z(0), Z(0), Z(0));
     AbiT<D> Jh;
     D Uv[3] = {D(0), D(0), D(0)}, Uw[3] = {D(0), D(0), D(0)}, invOm = D(0), chat = D(0);
-    DhRot<T> Rn = dh_rot(T(1), T(0), T(1), T(0));
-    V3<T> bn = mk3(T(0), T(0), T(0));
+    DhRot<TB> Rn = dh_rot(dcvt<TB>(T(1)), dcvt<TB>(T(0)), dcvt<TB>(T(1)), dcvt<TB>(T(0)));
+    V3<TB> bn = mk3(dcvt<TB>(T(0)), dcvt<TB>(T(0)), dcvt<TB>(T(0)));
     DhRot<Z> RnZ = dh_rot(Z(1), Z(0), Z(1), Z(0));
     V3<Z> bnZ = mk3(Z(0), Z(0), Z(0));
     D cn = D(1), sn = D(0);  // cos, sin of link i+1 in D
@@ -238,12 +293,20 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
             prefetch_l1(rp);
             prefetch_l1(rp + kAbaDh64 / 2);
             prefetch_l1(sc + (i - 1) * kDhConsts);
-            prefetch_l1(&ws[(size_t)(i - 1) * kAbaStateScalars * B + b]);
+            if constexpr (kExt) {
+                prefetch_l1(sdf + (i - 1) * kAbaDh64);
+                prefetch_l1(reinterpret_cast<const DF *>(ws) +
+                            (size_t)(i - 1) * kAbaBiasPairs * B + b);
+            } else {
+                prefetch_l1(&ws[(size_t)(i - 1) * kAbaStateScalars * B + b]);
+            }
         }
-        Wrench<T> Fh;
-        Fh.f = mk3(aba_get(ws, B, b, i, 0), aba_get(ws, B, b, i, 1), aba_get(ws, B, b, i, 2));
-        Fh.n = mk3(aba_get(ws, B, b, i, 3), aba_get(ws, B, b, i, 4), aba_get(ws, B, b, i, 5));
-        const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
+        Wrench<TB> Fh;
+        Fh.f = mk3(bias_get<TB>(ws, B, b, i, 0), bias_get<TB>(ws, B, b, i, 1),
+                   bias_get<TB>(ws, B, b, i, 2));
+        Fh.n = mk3(bias_get<TB>(ws, B, b, i, 3), bias_get<TB>(ws, B, b, i, 4),
+                   bias_get<TB>(ws, B, b, i, 5));
+        const TB c = bias_get<TB>(ws, B, b, i, 6), s = bias_get<TB>(ws, B, b, i, 7);
         const D *ri = sd + i * kAbaDh64;
         if (i == n - 1) {
             F.f = add3(F.f, Fh.f);
@@ -290,7 +353,9 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
             z.f = dh_mul(RnZ, zz.f);
             z.n = cross_add(bnZ, z.f, dh_mul(RnZ, zz.n));
         }
-        const D tau_hat = dsub_exact<D>(tau_i, F.n.z);
+        D tau_hat;
+        if constexpr (kExt) tau_hat = dcvt<D>(DF(tau_i) - F.n.z);
+        else tau_hat = dsub_exact<D>(tau_i, F.n.z);
         Uv[0] = Jh.Bm[2]; Uv[1] = Jh.Bm[5]; Uv[2] = Jh.Bm[8];
         Uw[0] = Jh.C.xz; Uw[1] = Jh.C.yz; Uw[2] = Jh.C.zz;
         const D Om = Jh.C.zz;
@@ -303,8 +368,14 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
         for (int k = 0; k < 8; ++k) aba_zput(wsz, B, b, i, k, vals[k]);
         // transform of link i, for the step to link i-1
         const T *Lt = sc + i * kDhConsts;
-        Rn = dh_rot(Lt[0], Lt[1], c, s);
-        bn = mk3(Lt[2], Lt[3], Lt[4]);
+        if constexpr (kExt) {
+            const DF *rf = sdf + i * kAbaDh64;
+            Rn = dh_rot(rf[0], rf[1], c, s);
+            bn = mk3(rf[2], rf[3], rf[4]);
+        } else {
+            Rn = dh_rot(Lt[0], Lt[1], c, s);
+            bn = mk3(Lt[2], Lt[3], Lt[4]);
+        }
         cn = dcvt<D>(c);
         sn = dcvt<D>(s);
         if constexpr (kZrec) {
@@ -337,7 +408,7 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
             prefetch_l1(rp + kAbaDh64 / 2);
             prefetch_l1(&wsz[(size_t)(i + 1) * kAbaSolveScalars * B + b]);
         }
-        const T c = aba_get(ws, B, b, i, 8), s = aba_get(ws, B, b, i, 9);
+        const TB c = bias_get<TB>(ws, B, b, i, 6), s = bias_get<TB>(ws, B, b, i, 7);
         DhRot<Z> R;
         V3<Z> bi;
         if constexpr (kZrec) {
@@ -382,8 +453,17 @@ __device__ __forceinline__ int aba_dh_instance(const T *sc, const D *sd, int n,
     return bad;
 }
 
+// Minimum resident threads per SM the launch bounds ask for (they cap the
+// registers per thread at 65536 / this).
+#ifndef RD_ABA_MIN_THREADS_PER_SM
+#define RD_ABA_MIN_THREADS_PER_SM 512
+#endif
+#ifndef RD_ABA_DHG_MIN_THREADS_PER_SM
+#define RD_ABA_DHG_MIN_THREADS_PER_SM 384
+#endif
+
 template <typename T, typename D, typename Z, int NMAX, int BLOCK, int TRIG>
-__global__ void __launch_bounds__(BLOCK, 512 / BLOCK)
+__global__ void __launch_bounds__(BLOCK, RD_ABA_MIN_THREADS_PER_SM / BLOCK)
 aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, D, NMAX> pc, int n, int B,
               const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
               T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
@@ -402,19 +482,20 @@ aba_dh_kernel(const __grid_constant__ AbaDhConsts<T, D, NMAX> pc, int n, int B,
 // pairs) in global memory, for what the parameter space does not take: chains
 // longer than 64 links, lengths not a multiple of 4, unaligned rows
 // (VEC = false). The sweeps prefetch each next link's constants, records and
-// workspace into L1.
-template <typename T, typename D, typename Z, int BLOCK, bool VEC>
-__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 8 ? 256 : 384) / BLOCK)
+// workspace into L1. TB: precision of the bias sweeps (T, or DF on sdf, the
+// records as double-float pairs).
+template <typename T, typename D, typename Z, int BLOCK, bool VEC, typename TB = T>
+__global__ void __launch_bounds__(BLOCK, (sizeof(T) == 8 ? 256 : RD_ABA_DHG_MIN_THREADS_PER_SM) / BLOCK)
 aba_dhg_kernel(const T *__restrict__ sc, const D *__restrict__ sd, int n, int B,
                const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ tau,
                T *__restrict__ qdd_out, int *__restrict__ status, T *__restrict__ ws,
-               Z *__restrict__ wsz, BaseParams<T> base)
+               Z *__restrict__ wsz, BaseParams<T> base, const DF *__restrict__ sdf)
 {
     const int b = blockIdx.x * BLOCK + threadIdx.x;
     if (b >= B) return;
     const size_t row = (size_t)b * (size_t)n;
-    const int bad = aba_dh_instance<T, D, Z, kTrigPoly, VEC, true>(
-        sc, sd, n, q + row, qd + row, tau + row, qdd_out + row, ws, wsz, B, b, base);
+    const int bad = aba_dh_instance<T, D, Z, kTrigPoly, VEC, true, TB>(
+        sc, sd, n, q + row, qd + row, tau + row, qdd_out + row, ws, wsz, B, b, base, sdf);
     if (status) status[b] = bad ? RD_WARN_SINGULAR : 0;
 }
 

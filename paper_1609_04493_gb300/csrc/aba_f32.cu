@@ -10,5 +10,5 @@ int rd_aba_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
 
 size_t rd_aba_ws_bytes_f32(int n, int B, int flags)
 {
-    return rdyn::aba_ws_bytes<float>(n, B, sizeof(float) == 4 && (flags & RD_ABA_SCANS_IN_DTYPE));
+    return rdyn::aba_ws_bytes<float>(n, B, flags);
 }

@@ -10,5 +10,5 @@ int rd_aba_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd,
 
 size_t rd_aba_ws_bytes_f64(int n, int B, int flags)
 {
-    return rdyn::aba_ws_bytes<double>(n, B, sizeof(double) == 4 && (flags & RD_ABA_SCANS_IN_DTYPE));
+    return rdyn::aba_ws_bytes<double>(n, B, flags);
 }

@@ -16,10 +16,29 @@ namespace {
 
 inline bool aba_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Bias sweeps in double-float (FP32 data): by flag, or for chains longer than
+// RD_ABA_EXTENDED_BIAS_LINKS unless RD_ABA_FP32_BIAS asks for FP32.
 template <typename T>
-size_t aba_ws_bytes(int n, int B, bool fp32_scans)
+bool aba_extended_bias(int n, int flags)
 {
-    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
+    if (sizeof(T) != 4 || (flags & RD_ABA_JOINT_FRAMES)) return false;
+    if (flags & RD_ABA_EXTENDED_BIAS) return true;
+    return n > RD_ABA_EXTENDED_BIAS_LINKS && !(flags & RD_ABA_FP32_BIAS);
+}
+
+// bytes of the sweep-1 state (F_hat, cos, sin per link)
+template <typename T>
+size_t aba_bias_bytes(int n, int B, bool extended)
+{
+    const int per = extended ? aba_bias_ws_scalars<T, DF>() : aba_bias_ws_scalars<T, T>();
+    return (size_t)n * per * (size_t)B * sizeof(T);
+}
+
+template <typename T>
+size_t aba_ws_bytes(int n, int B, int flags)
+{
+    const bool fp32_scans = sizeof(T) == 4 && (flags & RD_ABA_SCANS_IN_DTYPE);
+    const size_t a = aba_bias_bytes<T>(n, B, aba_extended_bias<T>(n, flags));
     const size_t a16 = (a + 255) & ~(size_t)255;
     return a16 + (size_t)n * kAbaSolveScalars * (size_t)B * (fp32_scans ? sizeof(T) : sizeof(double));
 }
@@ -104,10 +123,11 @@ int launch_aba_dh(const rd_model *m, int B, const void *q, const void *qd, const
     return launch_aba_dh_k<T, D, Z, 64, kTrigPoly>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
 
-template <typename T, typename D, typename Z, bool VEC>
+template <typename T, typename D, typename Z, bool VEC, typename TB = T>
 int launch_aba_dhg(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                    void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
 {
+    constexpr bool kExt = !std::is_same<TB, T>::value;
     constexpr int BLOCK = 64;
     const int n = m->n;
     double bb[18];
@@ -124,22 +144,30 @@ int launch_aba_dhg(const rd_model *m, int B, const void *q, const void *qd, cons
     const D *sd = nullptr;
     if constexpr (std::is_same<D, double>::value) sd = m->d_aba64;
     else sd = reinterpret_cast<const D *>(m->d_abadf);
-    const size_t a = (size_t)n * kAbaStateScalars * (size_t)B * sizeof(T);
+    const size_t a = aba_bias_bytes<T>(n, B, kExt);
     Z *wsz = reinterpret_cast<Z *>(static_cast<char *>(ws) + ((a + 255) & ~(size_t)255));
+    const DF *sdf = kExt ? reinterpret_cast<const DF *>(m->d_abadf) : nullptr;
+    if (kExt && !sdf) return rd_fail(RD_ERR_ARG, "aba_batch: model has no double-float records");
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
-    aba_dhg_kernel<T, D, Z, BLOCK, VEC><<<grid, BLOCK, 0, stream>>>(
+    aba_dhg_kernel<T, D, Z, BLOCK, VEC, TB><<<grid, BLOCK, 0, stream>>>(
         sc, sd, n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
-        static_cast<const T *>(tau), static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz, bp);
+        static_cast<const T *>(tau), static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz, bp,
+        sdf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return rd_cuda_fail(e, "aba global-constant kernel launch");
     return RD_OK;
 }
 
 template <typename T, typename D, typename Z>
-int launch_aba_dhg_v(bool vec, const rd_model *m, int B, const void *q, const void *qd,
+int launch_aba_dhg_v(bool vec, bool ext, const rd_model *m, int B, const void *q, const void *qd,
                      const void *tau, void *qdd, int *status, void *ws, const double *base18,
                      cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (ext)
+            return vec ? launch_aba_dhg<T, D, Z, true, DF>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+                       : launch_aba_dhg<T, D, Z, false, DF>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    }
     return vec ? launch_aba_dhg<T, D, Z, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
                : launch_aba_dhg<T, D, Z, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
@@ -150,14 +178,15 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
                  int flags, cudaStream_t s)
 {
     const bool fp32_scans = sizeof(T) == 4 && (flags & RD_ABA_SCANS_IN_DTYPE);
-    const size_t need = aba_ws_bytes<T>(m->n, B, fp32_scans);
+    const bool ext = aba_extended_bias<T>(m->n, flags);
+    const size_t need = aba_ws_bytes<T>(m->n, B, flags);
     if (!ws || ws_bytes < need)
         return rd_fail(RD_ERR_ARG, "aba_batch: needs a %zu-byte workspace (%zu given)", need,
                        ws_bytes);
     if (!aba_aligned16(ws)) return rd_fail(RD_ERR_ARG, "aba_batch: workspace not 16-byte aligned");
     const bool vec = m->n % 4 == 0 && aba_aligned16(q) && aba_aligned16(qd) &&
                      aba_aligned16(tau) && aba_aligned16(qdd);
-    if (vec && m->n <= 64 && !(flags & RD_ABA_JOINT_FRAMES)) {
+    if (vec && m->n <= 64 && !ext && !(flags & RD_ABA_JOINT_FRAMES)) {
         // common-normal frames, constants as a kernel parameter (aba_dh.cuh)
         if constexpr (sizeof(T) == 4) {
             if (!(flags & RD_ABA_FP64_UPDATE))
@@ -174,16 +203,22 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
         if constexpr (sizeof(T) == 4) {
             if (!(flags & RD_ABA_FP64_UPDATE)) {
                 if (fp32_scans)
-                    return launch_aba_dhg_v<T, DF, T>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
-                return launch_aba_dhg_v<T, DF, DF>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
+                    return launch_aba_dhg_v<T, DF, T>(vec, ext, m, B, q, qd, tau, qdd, status, ws, base18, s);
+                return launch_aba_dhg_v<T, DF, DF>(vec, ext, m, B, q, qd, tau, qdd, status, ws, base18, s);
             }
             if (fp32_scans)
-                return launch_aba_dhg_v<T, double, T>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
+                return launch_aba_dhg_v<T, double, T>(vec, ext, m, B, q, qd, tau, qdd, status, ws, base18, s);
         }
-        return launch_aba_dhg_v<T, double, double>(vec, m, B, q, qd, tau, qdd, status, ws, base18, s);
+        return launch_aba_dhg_v<T, double, double>(vec, ext, m, B, q, qd, tau, qdd, status, ws, base18, s);
     }
-    // joint frames (RD_ABA_JOINT_FRAMES), full 6x6 congruence (aba.cuh)
+    // joint frames (RD_ABA_JOINT_FRAMES), full 6x6 congruence (aba.cuh); its
+    // bias sweeps stay in FP32 for FP32 data, which meets the 1e-3 bar on qdd
+    // only up to RD_ABA_EXTENDED_BIAS_LINKS links
     if constexpr (sizeof(T) == 4) {
+        if (m->n > RD_ABA_EXTENDED_BIAS_LINKS)
+            return rd_fail(RD_ERR_RANGE,
+                           "aba_batch: RD_ABA_JOINT_FRAMES takes at most %d links for RD_F32 "
+                           "data (n = %d)", RD_ABA_EXTENDED_BIAS_LINKS, m->n);
         if (fp32_scans)
             return vec ? launch_aba_k<T, T, 64, true>(m, B, q, qd, tau, qdd, status, ws, base18, s)
                        : launch_aba_k<T, T, 64, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);

@@ -46,6 +46,11 @@ struct FleetArgs {
     // byte offsets of its T part ([link][10][lane]) and its solve part
     // ([link][8][lane])
     const long long *group_ws, *group_wz;
+    // the records as double-float pairs, and the number of leading groups of
+    // 32 whose forward-dynamics requests run the bias sweeps on them in
+    // double-float (FP32 data, chains beyond RD_ABA_EXTENDED_BIAS_LINKS)
+    const DF *records_df;
+    int ext_groups;
     int R;
     const T *q, *qd, *in2;    // in2: qdd (inverse) or tau (forward)
     T *out;                   // tau (inverse) or qdd (forward)
@@ -147,9 +152,17 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T, D> &a, int k)
         const int g = k >> 5;
         T *wt = reinterpret_cast<T *>(a.ws + a.group_ws[g]);
         D *wz = reinterpret_cast<D *>(a.ws + a.group_wz[g]);
-        const int bad = aba_dh_instance<T, D, D, kTrigPoly, false, true>(
-            sc, a.records + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off, a.out + off,
-            wt, wz, 32, k & 31, bp);
+        int bad = -1;
+        if constexpr (sizeof(T) == 4) {
+            if (g < a.ext_groups)
+                bad = aba_dh_instance<T, D, D, kTrigPoly, false, true, DF>(
+                    sc, a.records + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off,
+                    a.out + off, wt, wz, 32, k & 31, bp, a.records_df + lo * kAbaDh64);
+        }
+        if (bad < 0)
+            bad = aba_dh_instance<T, D, D, kTrigPoly, false, true>(
+                sc, a.records + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off,
+                a.out + off, wt, wz, 32, k & 31, bp);
         if (a.status) a.status[r] = bad ? 1 : 0;
     }
 }

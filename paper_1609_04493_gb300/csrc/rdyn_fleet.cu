@@ -38,6 +38,10 @@ struct rd_plan {
     int *order = nullptr, *req_robot = nullptr, *req_kind = nullptr, *counter = nullptr;
     long long *req_off = nullptr;
     long long *group_ws = nullptr, *group_wz = nullptr;  // per 32 sorted positions
+    // leading groups of 32 sorted positions whose forward-dynamics requests
+    // run the bias sweeps in double-float (FP32 plans; longest chain beyond
+    // RD_ABA_EXTENDED_BIAS_LINKS)
+    int ext_groups = 0;
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     int sms = 0;
@@ -192,17 +196,23 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
     });
     // forward-dynamics workspace per group of 32 sorted positions, laid out
     // [link][component][lane] so that a warp's accesses coalesce; sized by the
-    // group's longest forward-dynamics chain
+    // group's longest forward-dynamics chain. In FP32 plans a group whose
+    // longest chain exceeds RD_ABA_EXTENDED_BIAS_LINKS runs its bias sweeps in
+    // double-float (8 pairs per link instead of 10 scalars); being sorted
+    // first, such groups form a prefix.
     const int groups32 = (R + 31) / 32;
     std::vector<long long> gws(groups32, 0), gwz(groups32, 0);
     size_t ws = 0;
+    int ext_groups = 0;
     for (int g = 0; g < groups32; ++g) {
         size_t nmax = 0;
         for (int k = 32 * g; k < R && k < 32 * g + 32; ++k)
             if (kind[order[k]] == RD_REQ_FD) nmax = std::max(nmax, (size_t)f->n[robot[order[k]]]);
         if (!nmax) continue;
+        const bool ext = dtype == RD_F32 && nmax > RD_ABA_EXTENDED_BIAS_LINKS;
+        if (ext) ext_groups = g + 1;
         gws[g] = (long long)ws;
-        ws += (nmax * 10 * 32 * esz + 255) & ~(size_t)255;
+        ws += (nmax * (ext ? 16 : 10) * 32 * esz + 255) & ~(size_t)255;
         gwz[g] = (long long)ws;
         ws += (nmax * 8 * 32 * 8 + 255) & ~(size_t)255;
     }
@@ -230,6 +240,7 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
     if (e == cudaSuccess) e = cudaMalloc(&p->counter, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&p->ws, std::max<size_t>(ws, 16));
     p->ws_bytes = ws;
+    p->ext_groups = ext_groups;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     for (int k = 0; k < rd_plan::kSide && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
@@ -273,6 +284,8 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
     }
     if constexpr (std::is_same<D, double>::value) a.records = f->aba64;
     else a.records = f->abadf;
+    a.records_df = f->abadf;
+    a.ext_groups = p->ext_groups;
     a.robot_n = f->robot_n;
     a.robot_link = f->robot_link;
     a.order = p->order;
