@@ -419,6 +419,24 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
             return time_calls(torch, call, steps, 3, dist, sampler) / steps
 
         raw[f"n{n}_B{B}"] = {"n": n, "B": B, "t64": timed(rd.RD_ABA_FP64_UPDATE), "tdf": timed(0)}
+    # thread per instance against warp per instance (Sec. III-D scans) across
+    # batch sizes, double-float updates: microseconds [thread, warp, AUTO]
+    xo = {}
+    for n in (16, 64):
+        model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
+        for Bx in (256, 1024, 4096, 16384):
+            st = chaingen.make_states(Bx, n, seed=6100, kinds=("q", "qd", "tau"))
+            x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
+            ws = torch.empty(rd.aba_workspace_bytes(model, Bx, 0), dtype=torch.uint8, device=dev)
+            o = torch.empty_like(x[0])
+            steps = max(3, min(K, 20))
+            row = []
+            for fl in (rd.RD_ABA_THREAD_PER_INSTANCE, rd.RD_ABA_WARP_PER_INSTANCE, 0):
+                t = time_calls(torch, lambda k: rd.aba(model, *x, workspace=ws, out=o, flags=fl),
+                               steps, 3, dist, sampler)
+                row.append(t / steps * 1e6)
+            xo[f"n{n}_B{Bx}"] = [float(f"{t:.3g}") for t in row]
+    raw["crossover_us"] = xo
     return raw
 
 
@@ -429,6 +447,9 @@ def fd_report(raw, pk):
     df_frac: FP32-pipe issue time of the double-float kernel's instructions."""
     out = {}
     for name, r in raw.items():
+        if name == "crossover_us":
+            out[name] = r
+            continue
         nb = r["n"] * r["B"]
         t_exec = nb * (FD_EXEC_FLOP32_PER_LINK / pk.f32 + FD_EXEC_FLOP64_PER_LINK / pk.f64)
         t_alg = nb * (FD_FLOP32_PER_LINK / pk.f32 + FD_FLOP64_PER_LINK / pk.f64)
@@ -463,7 +484,7 @@ def crossover_section(torch, rd, chaingen, dev, dist, sampler, K):
     for n in (16, 100):
         raw[f"n{n}_B{BATCH}"] = {"n": n, "t": case(n, BATCH, rd.RD_VARIANT_AUTO)}
     for B in (1024, 2048, 4096, 8192):
-        raw[f"n{N_LINKS}_B{B}_us"] = [case(N_LINKS, B, v) * 1e6 for v in
+        raw[f"n{N_LINKS}_B{B}_us"] = [float(f"{case(N_LINKS, B, v) * 1e6:.3g}") for v in
                                       (rd.RD_VARIANT_AUTO, rd.RD_VARIANT_SERIAL_DH,
                                        rd.RD_VARIANT_SCAN(16))]
     return raw
@@ -537,8 +558,7 @@ def uneven_report(raw, pk):
     for name in ("persistent", "per_group", "df_persistent"):
         r = raw[name]
         floor = t_id + (t_df if name == "df_persistent" else t_fd)
-        out[name] = {"us": r["t"] * 1e6, "value": raw["count"] / r["t"], "frac": floor / r["t"],
-                     "sched": r["schedule"], "tune": r["tune"]}
+        out[name] = {"us": r["t"] * 1e6, "value": raw["count"] / r["t"], "frac": floor / r["t"]}
     out["launches_per_group"] = raw["groups"]
     return out
 
@@ -685,7 +705,7 @@ def run_ours(args):
         res["e2e"] = {"value": world * BATCH / te["inplace"], "unit": UNIT, "steps": Ke,
                       "h2d_bytes_per_step": 3 * BATCH * N_LINKS * 4,
                       "d2h_bytes_per_step": BATCH * N_LINKS * 4,
-                      "api": "rnea_batch_host", "host_sets": 2,
+                      "host_sets": 2,
                       "link_gbs": 4 * BATCH * N_LINKS * 4 / te["inplace"] / 1e9,
                       "staged_value": world * BATCH / te["staged"]}
     if "crossover" in raw:

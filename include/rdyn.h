@@ -82,6 +82,17 @@ enum rd_status {
 #define RD_ABA_EXTENDED_BIAS 0x8
 #define RD_ABA_FP32_BIAS 0x10
 #define RD_ABA_EXTENDED_BIAS_LINKS 64
+/* aba_batch flags: the mapping of instances to threads. One thread per
+ * instance runs the three sweeps of the recursion serially; one warp per
+ * instance (Sec. III-D) runs tau_bias by the scans of inverse dynamics across
+ * its lanes, the articulated-inertia recursion (Eq. abi) link by link with each
+ * link's update spread over 21 lanes, and the z_hat / c_hat and lambda / qdd
+ * recursions (Eqs. fd-bkwd-scan, fd-fwd-scan) as scans across its lanes. The
+ * warp mapping suits batches too small to fill the GPU with threads. Without
+ * either flag the library picks by the batch size and n. Not combinable with
+ * RD_ABA_JOINT_FRAMES or RD_ABA_SCANS_IN_DTYPE. */
+#define RD_ABA_WARP_PER_INSTANCE 0x20
+#define RD_ABA_THREAD_PER_INSTANCE 0x40
 
 /* Per-instance status word of aba_batch (0 = fine). */
 #define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */

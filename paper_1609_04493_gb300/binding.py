@@ -410,6 +410,8 @@ RD_ABA_FP64_UPDATE = 0x4
 RD_ABA_EXTENDED_BIAS = 0x8
 RD_ABA_FP32_BIAS = 0x10
 RD_ABA_EXTENDED_BIAS_LINKS = 64
+RD_ABA_WARP_PER_INSTANCE = 0x20
+RD_ABA_THREAD_PER_INSTANCE = 0x40
 
 
 def aba_workspace_bytes(model, B, dtype_code, flags=0):

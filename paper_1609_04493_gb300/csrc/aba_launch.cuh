@@ -172,6 +172,23 @@ int launch_aba_dhg_v(bool vec, bool ext, const rd_model *m, int B, const void *q
                : launch_aba_dhg<T, D, Z, false>(m, B, q, qd, tau, qdd, status, ws, base18, s);
 }
 
+// Warp per instance or thread per instance: by flag, else by the crossover
+// measured on GB300 (FP32 data, double-float updates, warp / thread time:
+// n = 64: 0.67 at B = 256, 0.85 at 1024, 3.2 at 4096; n = 100: 0.45 / 0.54 /
+// 2.0; n = 32: 0.94 / 1.12; n = 16: 1.7 at B = 256, never faster. With FP64
+// updates the warp's FP64 work saturates sooner: n = 64: 0.59 at 256, 1.08 at
+// 1024). The scans' fixed cost keeps short chains on threads.
+template <typename T>
+bool aba_use_warp(int n, int B, int flags)
+{
+    if (flags & RD_ABA_WARP_PER_INSTANCE) return true;
+    if (flags & (RD_ABA_THREAD_PER_INSTANCE | RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE))
+        return false;
+    if (n < 48) return false;
+    const bool fp64 = sizeof(T) == 8 || (flags & RD_ABA_FP64_UPDATE);
+    return B <= (fp64 ? 512 : 1024);
+}
+
 template <typename T>
 int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                  void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
@@ -184,6 +201,18 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
         return rd_fail(RD_ERR_ARG, "aba_batch: needs a %zu-byte workspace (%zu given)", need,
                        ws_bytes);
     if (!aba_aligned16(ws)) return rd_fail(RD_ERR_ARG, "aba_batch: workspace not 16-byte aligned");
+    if ((flags & RD_ABA_WARP_PER_INSTANCE) &&
+        (flags & (RD_ABA_THREAD_PER_INSTANCE | RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE)))
+        return rd_fail(RD_ERR_ARG, "aba_batch: RD_ABA_WARP_PER_INSTANCE excludes "
+                                   "RD_ABA_THREAD_PER_INSTANCE, RD_ABA_JOINT_FRAMES and "
+                                   "RD_ABA_SCANS_IN_DTYPE");
+    if (aba_use_warp<T>(m->n, B, flags)) {
+        if constexpr (sizeof(T) == 4)
+            return rd_aba_warp_f32(m, B, q, qd, tau, qdd, status, base18,
+                                   (flags & RD_ABA_FP64_UPDATE) != 0, ext, s);
+        else
+            return rd_aba_warp_f64(m, B, q, qd, tau, qdd, status, base18, s);
+    }
     const bool vec = m->n % 4 == 0 && aba_aligned16(q) && aba_aligned16(qd) &&
                      aba_aligned16(tau) && aba_aligned16(qdd);
     if (vec && m->n <= 64 && !ext && !(flags & RD_ABA_JOINT_FRAMES)) {

@@ -91,6 +91,12 @@ int rd_aba_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
 int rd_aba_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                         void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
                         int flags, cudaStream_t s);
+// forward dynamics with one warp per instance (aba_warp.cuh)
+int rd_aba_warp_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                    void *qdd, int *status, const double *base18, bool fp64_update,
+                    bool extended_bias, cudaStream_t s);
+int rd_aba_warp_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                    void *qdd, int *status, const double *base18, cudaStream_t s);
 size_t rd_aba_ws_bytes_f32(int n, int B, int flags);
 size_t rd_aba_ws_bytes_f64(int n, int B, int flags);
 int rd_build_chain(int n, const double *M, const double *S, const double *inertia,

@@ -15,6 +15,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 TOL = {"float32": 1e-3, "float64": 1e-8}
+AUTO = 1 << 30  # test-only marker: leave the mapping to the library
 
 
 def run(rd, n, B, dtype, seed=31, base=None, chain=None, status=None, flags=0):
@@ -26,10 +27,26 @@ def run(rd, n, B, dtype, seed=31, base=None, chain=None, status=None, flags=0):
     host = {k: st[k].astype(npdt) for k in st}
     dev = {k: torch.from_numpy(v).cuda() for k, v in host.items()}
     model = rd.Model(ch)
-    qdd = rd.aba(model, dev["q"], dev["qd"], dev["tau"], base=base, status=status, flags=flags)
+    # this file covers the thread-per-instance kernels (test_aba_warp_gpu.py the
+    # warp ones): pin the mapping unless the test asks for AUTO
+    if not flags & AUTO:
+        flags |= rd.RD_ABA_THREAD_PER_INSTANCE
+    qdd = rd.aba(model, dev["q"], dev["qd"], dev["tau"], base=base, status=status,
+                 flags=flags & ~AUTO)
     torch.cuda.synchronize()
     h64 = {k: v.astype(np.float64) for k, v in host.items()}
     return qdd.cpu().double().numpy(), ch, h64, model
+
+
+def test_aba_auto_mapping_matches_oracle(cuda_lib):
+    """Without a mapping flag the library takes one warp per instance for long
+    chains in small batches and one thread per instance otherwise; both agree
+    with the oracle."""
+    for n, B in ((64, 256), (100, 1024), (64, 2048), (16, 256)):
+        qdd, ch, h, _ = run(cuda_lib, n, B, "float32", seed=5, flags=AUTO)
+        idx = np.arange(0, B, max(1, B // 128))
+        ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
+        assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"], (n, B)
 
 
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
