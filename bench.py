@@ -350,11 +350,12 @@ class Peaks:
 
 
 def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
-    """Seconds per rnea_vjp call at n = 32 FP32: recompute at B = 8192 and
-    262144, store at 8192, and the two-warp split at 8192."""
+    """Seconds per rnea_vjp call at n = 32 FP32: recompute (the library's
+    mapping) at B = 4096, 8192 and 262144, store at 8192, and at 8192 each
+    mapping by flag: one thread, shared-memory state, 8 lanes, two warps."""
     raw = {}
-    for B, mode in ((8192, rd.RD_VJP_RECOMPUTE), (262144, rd.RD_VJP_RECOMPUTE),
-                    (8192, rd.RD_VJP_STORE)):
+    R = rd.RD_VJP_RECOMPUTE
+    for B, mode in ((4096, R), (8192, R), (262144, R), (8192, rd.RD_VJP_STORE)):
         sets = []
         nsets = 2 if B > 100000 else 8
         for r in range(nsets):
@@ -366,31 +367,35 @@ def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
             ws = torch.empty(rd.vjp_workspace_bytes(model, B, 0), dtype=torch.uint8, device=dev)
         steps = max(3, min(K, 200 if B < 100000 else 50))
 
-        def call(k):
-            x, o = sets[k % len(sets)]
-            rd.rnea_vjp(model, *x, mode=mode, workspace=ws, out=o)
+        def timed(md):
+            def call(k):
+                x, o = sets[k % len(sets)]
+                rd.rnea_vjp(model, *x, mode=md, workspace=ws, out=o)
+            return time_calls(torch, call, steps, 3, dist, sampler) / steps
 
         name = f"B{B}_{'store' if mode == rd.RD_VJP_STORE else 'recompute'}"
-        raw[name] = {"B": B, "mode": mode,
-                     "t": time_calls(torch, call, steps, 3, dist, sampler) / steps}
-        if B == 8192 and mode == rd.RD_VJP_RECOMPUTE:
-            def call2(k):
-                x, o = sets[k % len(sets)]
-                rd.rnea_vjp(model, *x, mode=mode | rd.RD_VJP_FLAG_TWO_WARPS, out=o)
-
-            raw[name]["t2"] = time_calls(torch, call2, steps, 3, dist, sampler) / steps
+        raw[name] = {"B": B, "mode": mode, "t": timed(mode)}
+        if B == 8192 and mode == R:
+            raw[name]["alt"] = {
+                nm: timed(R | fl) for nm, fl in (("one_us", rd.RD_VJP_FLAG_ONE_THREAD),
+                                                 ("smem_us", rd.RD_VJP_FLAG_SHARED_STATE),
+                                                 ("lanes_us", rd.RD_VJP_FLAG_LANES),
+                                                 ("pair_us", rd.RD_VJP_FLAG_TWO_WARPS))}
     return raw
 
 
 def adjoint_report(raw, pk):
-    """frac: the kernel's executed arithmetic (FMA = 2) over the FP32 peak."""
+    """frac: the adjoint's work per link, the 621 flop (FMA = 2) of the
+    store-mode kernel that re-derives nothing, over the FP32 peak; re-deriving
+    the state (772 per link) or scanning across lanes costs more than that."""
     out = {}
     for name, r in raw.items():
-        fpl = VJP_FLOP_PER_LINK[r["mode"]]
-        out[name] = {"us": r["t"] * 1e6, "value": r["B"] / r["t"], "flop_per_link": fpl,
+        fpl = VJP_FLOP_PER_LINK[1]
+        out[name] = {"us": r["t"] * 1e6, "value": r["B"] / r["t"],
                      "frac": r["B"] * N_LINKS * fpl / r["t"] / pk.f32}
-        if "t2" in r:
-            out[name]["two_warps_us"] = r["t2"] * 1e6
+        for k, t in r.get("alt", {}).items():
+            out[name][k] = t * 1e6
+    out["flop_per_link"] = VJP_FLOP_PER_LINK[1]
     return out
 
 
@@ -456,7 +461,7 @@ def fd_report(raw, pk):
         t_df = nb * FD_DF_EXEC_FP32_INST_PER_LINK / pk.i32
         out[name] = {"us": r["t64"] * 1e6, "value": r["B"] / r["t64"], "frac": t_exec / r["t64"],
                      "frac_alg": t_alg / r["t64"], "df_us": r["tdf"] * 1e6,
-                     "df_value": r["B"] / r["tdf"], "df_frac": t_df / r["tdf"]}
+                     "df_frac": t_df / r["tdf"]}
     return out
 
 
@@ -496,7 +501,7 @@ def crossover_report(raw, pk):
     out = {}
     for name, r in raw.items():
         if isinstance(r, dict):
-            out[name] = {"us": r["t"] * 1e6, "value": BATCH / r["t"],
+            out[name] = {"us": r["t"] * 1e6,
                          "frac": BATCH * r["n"] * ALGO_FLOP_PER_LINK / r["t"] / pk.f32}
         else:
             out[name] = r

@@ -259,6 +259,19 @@ enum rd_vjp_mode {
  * states, the case where the split measured faster. Setting both is RD_ERR_ARG. */
 #define RD_VJP_FLAG_TWO_WARPS 0x800
 #define RD_VJP_FLAG_ONE_THREAD 0x400
+/* OR-able into the mode of rnea_vjp, for FP32 in RD_VJP_RECOMPUTE (or AUTO) on
+ * whole 16-byte chunks: spread each instance over RD_VJP_LANES_OF(flags) lanes
+ * (4 or 8; 8 if unset), which scan the forward recursion with the adjoint
+ * weight as a third channel and the reverse recursion as affine segment maps
+ * (Sec. III), for batches too small to fill the GPU with one thread per
+ * instance. Without it the library picks by the batch size. */
+#define RD_VJP_FLAG_LANES 0x100
+#define RD_VJP_FLAG_LANES4 0x200
+/* OR-able into the mode of rnea_vjp, FP32, n % 4 == 0, n <= 64, recompute or
+ * AUTO: one thread per instance that keeps V, dV, Fb, cos and sin of every link
+ * in the block's shared memory instead of re-deriving them in the reverse
+ * sweep (no workspace). Without it the library picks by the batch size. */
+#define RD_VJP_FLAG_SHARED_STATE 0x4000
 
 /*
  * rnea_vjp -- vector-Jacobian product of inverse dynamics for B states:

@@ -33,6 +33,9 @@ RD_VJP_RECOMPUTE = 2
 RD_VJP_FLAG_JOINT_FRAMES = 0x2000
 RD_VJP_FLAG_TWO_WARPS = 0x800
 RD_VJP_FLAG_ONE_THREAD = 0x400
+RD_VJP_FLAG_LANES = 0x100
+RD_VJP_FLAG_LANES4 = 0x200
+RD_VJP_FLAG_SHARED_STATE = 0x4000
 
 
 def RD_VARIANT_SCAN(lanes):

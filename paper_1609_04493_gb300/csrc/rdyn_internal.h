@@ -91,6 +91,10 @@ int rd_aba_dispatch_f32(const rd_model *m, int B, const void *q, const void *qd,
 int rd_aba_dispatch_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                         void *qdd, int *status, void *ws, size_t ws_bytes, const double *base18,
                         int flags, cudaStream_t s);
+// the adjoint with L lanes per instance (rnea_vjp_lane.cuh), FP32
+int rd_vjp_lane_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                    const void *w, void *gq, void *gqd, void *gqdd, const double *base18,
+                    bool fast_trig, int lanes, cudaStream_t s);
 // forward dynamics with one warp per instance (aba_warp.cuh)
 int rd_aba_warp_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                     void *qdd, int *status, const double *base18, bool fp64_update,

@@ -29,7 +29,9 @@
 
 namespace rdyn {
 
-enum VjpMode { kVjpStore = 0, kVjpRecompute = 1 };
+// kVjpStoreShared: as kVjpStore, with the 20 scalars per link in the block's
+// shared memory instead of a workspace (common-normal kernel, small batches).
+enum VjpMode { kVjpStore = 0, kVjpRecompute = 1, kVjpStoreShared = 2 };
 constexpr int kVjpStateScalars = 20;
 
 // J u = (p, c x p + I_c u_w), p = m (u_v + u_w x c)  (spatial inertia about the

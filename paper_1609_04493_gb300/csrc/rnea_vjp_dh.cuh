@@ -47,6 +47,22 @@ rnea_vjp_dh_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int
                    T *__restrict__ gqdd, T *__restrict__ ws, BaseParams<T> base)
 {
     const T *sc = pc.c;
+    // kVjpStoreShared: the per-link state in shared memory, [link][k][thread]
+    extern __shared__ __align__(16) unsigned char vjp_smem[];
+    T *sst = reinterpret_cast<T *>(vjp_smem);
+    constexpr bool kStored = MODE == kVjpStore || MODE == kVjpStoreShared;
+    auto st_put = [&](int i, int k, T v) {
+        if constexpr (MODE == kVjpStoreShared)
+            sst[((size_t)i * kVjpStateScalars + k) * BLOCK + threadIdx.x] = v;
+        else
+            ws_put(ws, B, blockIdx.x * BLOCK + threadIdx.x, i, k, v);
+    };
+    auto st_get = [&](int i, int k) -> T {
+        if constexpr (MODE == kVjpStoreShared)
+            return sst[((size_t)i * kVjpStateScalars + k) * BLOCK + threadIdx.x];
+        else
+            return ws_get(ws, B, blockIdx.x * BLOCK + threadIdx.x, i, k);
+    };
     const int b = blockIdx.x * BLOCK + threadIdx.x;
     if (b >= B) return;
     const size_t row = (size_t)b * (size_t)n;
@@ -84,13 +100,13 @@ rnea_vjp_dh_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int
             const DhRot<T> R = dh_rot(X.ca, X.sa, c, s);
             x = dh_forward(R, X.b, cqd.v[j], cqdd.v[j], x);
             fb_forward_dh(R, X.b, cw.v[j], fbv, fbw);
-            if constexpr (MODE == kVjpStore) {
+            if constexpr (kStored) {
                 const T vals[kVjpStateScalars] = {x.v.x,  x.v.y,  x.v.z,  x.w.x,  x.w.y,
                                                   x.w.z,  x.a.x,  x.a.y,  x.a.z,  x.al.x,
                                                   x.al.y, x.al.z, fbv.x,  fbv.y,  fbv.z,
                                                   fbw.x,  fbw.y,  fbw.z,  c,      s};
 #pragma unroll
-                for (int k = 0; k < kVjpStateScalars; ++k) ws_put(ws, B, b, i, k, vals[k]);
+                for (int k = 0; k < kVjpStateScalars; ++k) st_put(i, k, vals[k]);
             }
         }
         cq = nq;
@@ -130,15 +146,15 @@ rnea_vjp_dh_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int
             DhLink<T> L;
             load_dh(sc + i * kDhConsts, L);
             T s, c;
-            if constexpr (MODE == kVjpStore) {
-                x.v = mk3(ws_get(ws, B, b, i, 0), ws_get(ws, B, b, i, 1), ws_get(ws, B, b, i, 2));
-                x.w = mk3(ws_get(ws, B, b, i, 3), ws_get(ws, B, b, i, 4), ws_get(ws, B, b, i, 5));
-                x.a = mk3(ws_get(ws, B, b, i, 6), ws_get(ws, B, b, i, 7), ws_get(ws, B, b, i, 8));
-                x.al = mk3(ws_get(ws, B, b, i, 9), ws_get(ws, B, b, i, 10), ws_get(ws, B, b, i, 11));
-                fbv = mk3(ws_get(ws, B, b, i, 12), ws_get(ws, B, b, i, 13), ws_get(ws, B, b, i, 14));
-                fbw = mk3(ws_get(ws, B, b, i, 15), ws_get(ws, B, b, i, 16), ws_get(ws, B, b, i, 17));
-                c = ws_get(ws, B, b, i, 18);
-                s = ws_get(ws, B, b, i, 19);
+            if constexpr (kStored) {
+                x.v = mk3(st_get(i, 0), st_get(i, 1), st_get(i, 2));
+                x.w = mk3(st_get(i, 3), st_get(i, 4), st_get(i, 5));
+                x.a = mk3(st_get(i, 6), st_get(i, 7), st_get(i, 8));
+                x.al = mk3(st_get(i, 9), st_get(i, 10), st_get(i, 11));
+                fbv = mk3(st_get(i, 12), st_get(i, 13), st_get(i, 14));
+                fbw = mk3(st_get(i, 15), st_get(i, 16), st_get(i, 17));
+                c = st_get(i, 18);
+                s = st_get(i, 19);
             } else {
                 dh_trig<T, TRIG>(cq.v[j] + L.th0, &s, &c);
             }

@@ -93,7 +93,20 @@ int launch_vjp_dh_k(const rd_model *m, int B, const void *q, const void *qd, con
     for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (T)m->host_dh64[k];
     for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = T(0);
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
-    rnea_vjp_dh_kernel<T, NMAX, BLOCK, MODE, TRIG><<<grid, BLOCK, 0, stream>>>(
+    size_t smem = 0;
+    if constexpr (MODE == kVjpStoreShared) {
+        static std::atomic<uint64_t> configured{0};
+        smem = (size_t)m->n * kVjpStateScalars * BLOCK * sizeof(T);
+        const uint64_t bit = 1ull << (m->device & 63);
+        if (smem > 48 * 1024 && !(configured.load() & bit)) {
+            cudaError_t e = cudaFuncSetAttribute(rnea_vjp_dh_kernel<T, NMAX, BLOCK, MODE, TRIG>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 vjp_max_smem(m->device));
+            if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+            configured.fetch_or(bit);
+        }
+    }
+    rnea_vjp_dh_kernel<T, NMAX, BLOCK, MODE, TRIG><<<grid, BLOCK, smem, stream>>>(
         pc, m->n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
         static_cast<const T *>(qdd), static_cast<const T *>(w), static_cast<T *>(gq),
         static_cast<T *>(gqd), static_cast<T *>(gqdd), static_cast<T *>(ws), bp);
@@ -128,18 +141,38 @@ int launch_vjp_pair_k(const rd_model *m, int B, const void *q, const void *qd, c
     return RD_OK;
 }
 
-// split: > 0 two warps per instance, < 0 one thread, 0 the library's choice
+// split: 1 two warps per instance, 2 one thread with the state in shared
+// memory, -1 one thread re-deriving it, 0 the library's choice; lanes: lanes
+// per instance for the lane-parallel kernel (0: not asked for)
 template <typename T, int MODE, int TRIG>
 int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                   const void *w, void *gq, void *gqd, void *gqdd, void *ws,
-                  const double *base18, int split, cudaStream_t s)
+                  const double *base18, int split, int lanes, cudaStream_t s)
 {
     if constexpr (sizeof(T) == 4 && MODE == kVjpRecompute) {
-        // CUDA-graph timings: n = 100, B = 8192: 40.6 us split, 44.8 one thread;
-        // n = 32, B = 8192: 13.2 vs 12.8; n = 16: 7.9 vs 6.9. A small batch takes
-        // the latency of one instance's motion and wrench recursion, which the
-        // split leaves on one warp; only long chains gain.
-        if (split > 0 || (split == 0 && m->n > 64 && B <= 8192)) {
+        // The library's choice for small batches, from CUDA-graph timings on
+        // GB300 (8 rotating input sets; microseconds one thread / shared state /
+        // 8 lanes / two warps): n = 16, B = 8192: 7.97 / 7.53 / 17.0 / 8.96;
+        // n = 32, B = 1024: 13.6 / 12.7 / 10.4 / 12.5, B = 4096: 13.6 / 12.7 /
+        // 11.3 / 13.5, B = 8192: 13.9 / 13.5 / 19.1 / 14.2; n = 64, B = 8192:
+        // 26.8 / 45.0 / 57.7 / 25.8; n = 100, B = 8192: 45.8 / - / 201 / 41.9.
+        if (split == 0 && lanes == 0) {
+            const int n = m->n;
+            if (n > 16 && n <= 32 && B <= 4096) lanes = 8;
+            else if (n <= 32 && B <= 8192) split = 2;
+            else if (n > 32 && B <= 8192) split = 1;
+        }
+        if (lanes > 0)
+            return rd_vjp_lane_f32(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, TRIG == kTrigSfu,
+                                   lanes, s);
+        if (split == 2) {  // state of every link in shared memory, 32-thread blocks
+            if (m->n <= 32)
+                return launch_vjp_dh_k<T, 32, 32, kVjpStoreShared, TRIG>(m, B, q, qd, qdd, w, gq, gqd,
+                                                                         gqdd, ws, base18, s);
+            return launch_vjp_dh_k<T, 64, 32, kVjpStoreShared, TRIG>(m, B, q, qd, qdd, w, gq, gqd,
+                                                                     gqdd, ws, base18, s);
+        }
+        if (split == 1) {
             if (m->n <= 32)
                 return launch_vjp_pair_k<32, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
             return launch_vjp_pair_k<128, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
@@ -159,18 +192,24 @@ int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const
 template <typename T, int MODE>
 int launch_vjp_any(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    const void *w, void *gq, void *gqd, void *gqdd, void *ws,
-                   const double *base18, bool fast, bool joint_frames, int split,
+                   const double *base18, bool fast, bool joint_frames, int split, int lanes,
                    cudaStream_t s)
 {
     const bool dh = !joint_frames && m->n % 4 == 0 && m->n <= 128 && vjp_aligned16(q) &&
                     vjp_aligned16(qd) && vjp_aligned16(qdd) && vjp_aligned16(w) &&
                     vjp_aligned16(gq) && vjp_aligned16(gqd) && vjp_aligned16(gqdd);
+    if (split == 2 && (!dh || MODE != kVjpRecompute))
+        return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_SHARED_STATE needs recompute (or AUTO) "
+                                   "mode and 16-byte aligned rows");
+    if (lanes && (!dh || sizeof(T) != 4 || MODE != kVjpRecompute))
+        return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_LANES needs FP32 data in recompute mode, "
+                                   "n %% 4 == 0, n <= 128 and 16-byte aligned rows");
     if (dh) {
         if (sizeof(T) == 4 && fast)
             return launch_vjp_dh<T, MODE, kTrigSfu>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18,
-                                                    split, s);
+                                                    split, lanes, s);
         return launch_vjp_dh<T, MODE, kTrigPoly>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18,
-                                                 split, s);
+                                                 split, lanes, s);
     }
     return launch_vjp_mode<T, MODE>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast, s);
 }
@@ -184,7 +223,18 @@ int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
     const bool joint_frames = (mode & RD_VJP_FLAG_JOINT_FRAMES) != 0;
     if ((mode & RD_VJP_FLAG_TWO_WARPS) && (mode & RD_VJP_FLAG_ONE_THREAD))
         return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_TWO_WARPS and RD_VJP_FLAG_ONE_THREAD both set");
-    const int split = (mode & RD_VJP_FLAG_TWO_WARPS) ? 1 : (mode & RD_VJP_FLAG_ONE_THREAD) ? -1 : 0;
+    int split = (mode & RD_VJP_FLAG_TWO_WARPS) ? 1 : (mode & RD_VJP_FLAG_ONE_THREAD) ? -1 : 0;
+    if (mode & RD_VJP_FLAG_SHARED_STATE) {
+        if (split != 0 || sizeof(T) != 4 || m->n > 64 || m->n % 4 != 0 ||
+            (mode & (RD_VJP_FLAG_LANES | RD_VJP_FLAG_LANES4 | RD_VJP_FLAG_JOINT_FRAMES)))
+            return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_SHARED_STATE needs FP32, n %% 4 == 0, "
+                                       "n <= 64 and no other mapping flag");
+        split = 2;
+    }
+    const int lanes = (mode & RD_VJP_FLAG_LANES4) ? 4 : (mode & RD_VJP_FLAG_LANES) ? 8 : 0;
+    if (lanes && (split != 0 || joint_frames))
+        return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_LANES excludes RD_VJP_FLAG_TWO_WARPS, "
+                                   "RD_VJP_FLAG_ONE_THREAD and RD_VJP_FLAG_JOINT_FRAMES");
     mode &= 0xff;
     const size_t need = (size_t)m->n * kVjpStateScalars * (size_t)B * sizeof(T);
     if (mode == RD_VJP_AUTO) {
@@ -194,16 +244,18 @@ int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
         mode = (sizeof(T) == 8 && ws && ws_bytes >= need) ? RD_VJP_STORE : RD_VJP_RECOMPUTE;
     }
     if (mode == RD_VJP_STORE) {
+        if (lanes)
+            return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_LANES runs in recompute mode only");
         if (!ws || ws_bytes < need)
             return rd_fail(RD_ERR_ARG, "rnea_vjp: store mode needs a %zu-byte workspace (%zu given)",
                            need, ws_bytes);
         if (!vjp_aligned16(ws)) return rd_fail(RD_ERR_ARG, "rnea_vjp: workspace not 16-byte aligned");
         return launch_vjp_any<T, kVjpStore>(m, B, q, qd, qdd, w, gq, gqd, gqdd, ws, base18, fast,
-                                            joint_frames, split, s);
+                                            joint_frames, split == 2 ? 2 : split, 0, s);
     }
     if (mode == RD_VJP_RECOMPUTE)
         return launch_vjp_any<T, kVjpRecompute>(m, B, q, qd, qdd, w, gq, gqd, gqdd, nullptr,
-                                                base18, fast, joint_frames, split, s);
+                                                base18, fast, joint_frames, split, lanes, s);
     return rd_fail(RD_ERR_ARG, "rnea_vjp: unknown mode %d", mode);
 }
 

@@ -28,8 +28,8 @@ def test_fractions_are_work_over_time_at_the_sampled_clock():
     t = 1e-5
     adj = bench.adjoint_report({"B8192_recompute": {"B": 8192, "mode": 2, "t": t}}, pk)
     r = adj["B8192_recompute"]
-    assert abs(r["frac"] - 8192 * 32 * 772 / t / pk.f32) < 1e-12
-    assert r["frac"] < 1.0 or t < 8192 * 32 * 772 / pk.f32
+    assert adj["flop_per_link"] == 621
+    assert abs(r["frac"] - 8192 * 32 * 621 / t / pk.f32) < 1e-12
     fd = bench.fd_report({"n64_B16384": {"n": 64, "B": 16384, "t64": 6e-4, "tdf": 3e-4}}, pk)
     f = fd["n64_B16384"]
     nb = 64 * 16384

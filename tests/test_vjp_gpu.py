@@ -135,9 +135,11 @@ def test_vjp_full_size_sampled(cuda_lib):
 # ---- common-normal frames (rows with n % 4 == 0 and 16-byte alignment)
 
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 2 | 0x400])
 @pytest.mark.parametrize("n", [4, 8, 12, 64, 100, 128])
 def test_vjp_common_normal_frames_match_complex_step(cuda_lib, n, dtype, mode):
+    """Store, recompute (the library's mapping for this batch) and recompute
+    with one thread per instance (RD_VJP_FLAG_ONE_THREAD = 0x400)."""
     g, ref, _, _ = run(cuda_lib, n, 150, dtype, mode, seed=13)
     err = grad_err(g, ref)
     assert err <= TOL[dtype], f"n={n} {dtype} mode={mode}: {err:.3e}"
@@ -245,3 +247,135 @@ def test_vjp_split_flags_conflict(cuda_lib):
             cuda_lib.RD_VJP_FLAG_ONE_THREAD)
     with pytest.raises(cuda_lib.RdError):
         cuda_lib.rnea_vjp(model, x, x, x, x, mode=mode)
+
+
+# ---- lanes per instance (RD_VJP_FLAG_LANES): forward and reverse sweeps as
+# scans across the lanes of each instance
+
+def _lane_flag(rd, lanes):
+    return rd.RD_VJP_RECOMPUTE | (rd.RD_VJP_FLAG_LANES4 if lanes == 4 else rd.RD_VJP_FLAG_LANES)
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64, 100, 128])
+@pytest.mark.parametrize("B", [1, 31])
+def test_vjp_lanes_match_complex_step(cuda_lib, n, B, lanes):
+    g, ref, _, _ = run(cuda_lib, n, B, "float32", _lane_flag(cuda_lib, lanes), seed=17)
+    err = grad_err(g, ref)
+    assert err <= TOL["float32"], f"n={n} B={B} lanes={lanes}: {err:.3e}"
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_vjp_lanes_workload_sampled(cuda_lib, lanes):
+    """n = 32, B = 8192 (the adjoint workload): every 32nd instance against the
+    oracle, and all of them within 1e-4 of one thread per instance."""
+    import torch
+
+    n, B = 32, 8192
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=5000, kinds=("q", "qd", "qdd", "w"))
+    x = [torch.from_numpy(st[k]).float().cuda() for k in ("q", "qd", "qdd", "w")]
+    model = cuda_lib.Model(ch)
+    g = cuda_lib.rnea_vjp(model, *x, mode=_lane_flag(cuda_lib, lanes))
+    h = cuda_lib.rnea_vjp(model, *x, mode=cuda_lib.RD_VJP_RECOMPUTE | cuda_lib.RD_VJP_FLAG_ONE_THREAD)
+    torch.cuda.synchronize()
+    idx = np.arange(0, B, 32)
+    ref = oracle.rnea_grad(ch, *(a.cpu().double().numpy()[idx] for a in x))
+    assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+    assert grad_err([a.cpu().numpy() for a in g], [b.cpu().numpy() for b in h]) <= 1e-4
+
+
+def test_vjp_lanes_large_batch_sampled(cuda_lib):
+    """B = 262144 at n = 32 with 8 lanes per instance: sampled against the oracle."""
+    import torch
+
+    n, B = 32, 262144
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=5001, kinds=("q", "qd", "qdd", "w"))
+    x = [torch.from_numpy(st[k]).float().cuda() for k in ("q", "qd", "qdd", "w")]
+    g = cuda_lib.rnea_vjp(cuda_lib.Model(ch), *x, mode=_lane_flag(cuda_lib, 8))
+    torch.cuda.synchronize()
+    idx = np.concatenate([np.arange(0, B, 1024), np.arange(B - 8, B)])
+    ref = oracle.rnea_grad(ch, *(a.cpu().double().numpy()[idx] for a in x))
+    assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_vjp_lanes_base_motion_wrench_and_fast_trig(cuda_lib, lanes):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    for n in (12, 32):
+        g, ref, _, _ = run(cuda_lib, n, 45, "float32", _lane_flag(cuda_lib, lanes), seed=23,
+                           base=base)
+        assert grad_err(g, ref) <= TOL["float32"], n
+    g, ref, _, _ = run(cuda_lib, 32, 45, "float32",
+                       _lane_flag(cuda_lib, lanes) | cuda_lib.RD_FLAG_FAST_TRIG, seed=24)
+    assert grad_err(g, ref) <= TOL["float32"]
+
+
+def test_vjp_lanes_reject_what_they_do_not_cover(cuda_lib):
+    import torch
+
+    lanes = cuda_lib.RD_VJP_FLAG_LANES
+    model = cuda_lib.Model(chaingen.make_chain(6))  # n % 4 != 0
+    x = torch.zeros((4, 6), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(model, x, x, x, x, mode=cuda_lib.RD_VJP_RECOMPUTE | lanes)
+    model8 = cuda_lib.Model(chaingen.make_chain(8))
+    y = torch.zeros((4, 8), device="cuda", dtype=torch.float64)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(model8, y, y, y, y, mode=cuda_lib.RD_VJP_RECOMPUTE | lanes)
+    z = torch.zeros((4, 8), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(model8, z, z, z, z, mode=cuda_lib.RD_VJP_STORE | lanes)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(model8, z, z, z, z,
+                          mode=cuda_lib.RD_VJP_RECOMPUTE | lanes | cuda_lib.RD_VJP_FLAG_TWO_WARPS)
+
+
+# ---- one thread per instance with the forward state in shared memory
+# (RD_VJP_FLAG_SHARED_STATE)
+
+@pytest.mark.parametrize("n", [4, 16, 32, 64])
+@pytest.mark.parametrize("B", [1, 31, 300])
+def test_vjp_shared_state_matches_complex_step(cuda_lib, n, B):
+    mode = cuda_lib.RD_VJP_RECOMPUTE | cuda_lib.RD_VJP_FLAG_SHARED_STATE
+    g, ref, _, _ = run(cuda_lib, n, B, "float32", mode, seed=19)
+    assert grad_err(g, ref) <= TOL["float32"], f"n={n} B={B}"
+
+
+def test_vjp_shared_state_workload_equals_store_mode(cuda_lib):
+    """n = 32, B = 8192: the same arithmetic as the workspace store mode, so
+    the same result to the last bit; sampled against the oracle."""
+    import torch
+
+    n, B = 32, 8192
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=5002, kinds=("q", "qd", "qdd", "w"))
+    x = [torch.from_numpy(st[k]).float().cuda() for k in ("q", "qd", "qdd", "w")]
+    model = cuda_lib.Model(ch)
+    g = cuda_lib.rnea_vjp(model, *x, mode=cuda_lib.RD_VJP_RECOMPUTE | cuda_lib.RD_VJP_FLAG_SHARED_STATE)
+    h = cuda_lib.rnea_vjp(model, *x, mode=cuda_lib.RD_VJP_STORE)
+    torch.cuda.synchronize()
+    for a, b in zip(g, h):
+        assert torch.equal(a, b)
+    idx = np.arange(0, B, 64)
+    ref = oracle.rnea_grad(ch, *(a.cpu().double().numpy()[idx] for a in x))
+    assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+
+
+def test_vjp_shared_state_rejects_what_it_does_not_cover(cuda_lib):
+    import torch
+
+    flag = cuda_lib.RD_VJP_FLAG_SHARED_STATE
+    m100 = cuda_lib.Model(chaingen.make_chain(100))
+    x = torch.zeros((4, 100), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(m100, x, x, x, x, mode=cuda_lib.RD_VJP_RECOMPUTE | flag)
+    m8 = cuda_lib.Model(chaingen.make_chain(8))
+    z = torch.zeros((4, 8), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(m8, z, z, z, z, mode=cuda_lib.RD_VJP_STORE | flag)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(m8, z, z, z, z, mode=cuda_lib.RD_VJP_RECOMPUTE | flag |
+                          cuda_lib.RD_VJP_FLAG_LANES)
