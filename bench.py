@@ -142,14 +142,16 @@ def parse_args():
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
     p.add_argument("--kernel-only",
-                   choices=["f32", "f64", "f64df", "host", "vjp", "aba", "aba64", "fleet"],
+                   choices=["f32", "f64", "f64df", "host", "vjp", "vjplane", "aba", "aba64",
+                            "abawarp", "fleet"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
                         "arithmetic; host: rnea_batch_host on pinned FP32 arrays, the same "
-                        "size; vjp: adjoint n=32 B=8192; "
-                        "aba: forward dynamics n=64 B=16384 (double-float updates; aba64: "
-                        "FP64 updates); fleet: 20000 mixed requests)")
+                        "size; vjp: adjoint n=32 B=8192; vjplane: adjoint n=32 B=4096, 8 lanes "
+                        "per instance; aba: forward dynamics n=64 B=16384 (double-float updates; "
+                        "aba64: FP64 updates); abawarp: forward dynamics n=64 B=1024, one warp per "
+                        "instance; fleet: 20000 mixed requests)")
     return p.parse_args()
 
 
@@ -828,18 +830,24 @@ def run_kernel_only(args):
         res = torch.empty_like(host[0]).pin_memory()
         for _ in range(calls):
             rd.rnea_host(model, *host, out=res)
-    elif args.kernel_only == "vjp":
+    elif args.kernel_only in ("vjp", "vjplane"):
+        lanes = args.kernel_only == "vjplane"
+        Bv = 4096 if lanes else 8192
+        mode = rd.RD_VJP_RECOMPUTE | (rd.RD_VJP_FLAG_LANES if lanes else rd.RD_VJP_FLAG_ONE_THREAD)
         model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
-        st = chaingen.make_states(8192, N_LINKS, seed=5000, kinds=("q", "qd", "qdd", "w"))
+        st = chaingen.make_states(Bv, N_LINKS, seed=5000, kinds=("q", "qd", "qdd", "w"))
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]
         for _ in range(calls):
-            res = rd.rnea_vjp(model, *x, mode=rd.RD_VJP_RECOMPUTE)[0]
-    elif args.kernel_only in ("aba", "aba64"):
-        flags = rd.RD_ABA_FP64_UPDATE if args.kernel_only == "aba64" else 0
+            res = rd.rnea_vjp(model, *x, mode=mode)[0]
+    elif args.kernel_only in ("aba", "aba64", "abawarp"):
+        flags = {"aba": rd.RD_ABA_THREAD_PER_INSTANCE,
+                 "aba64": rd.RD_ABA_FP64_UPDATE | rd.RD_ABA_THREAD_PER_INSTANCE,
+                 "abawarp": rd.RD_ABA_WARP_PER_INSTANCE}[args.kernel_only]
+        Ba = 1024 if args.kernel_only == "abawarp" else 16384
         model = rd.Model(chaingen.make_chain(64, seed=chaingen.BASE_SEED))
-        st = chaingen.make_states(16384, 64, seed=6000, kinds=("q", "qd", "tau"))
+        st = chaingen.make_states(Ba, 64, seed=6000, kinds=("q", "qd", "tau"))
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
-        ws = torch.empty(rd.aba_workspace_bytes(model, 16384, 0, flags), dtype=torch.uint8,
+        ws = torch.empty(rd.aba_workspace_bytes(model, Ba, 0, flags), dtype=torch.uint8,
                          device=dev)
         for _ in range(calls):
             res = rd.aba(model, *x, workspace=ws, flags=flags)
