@@ -426,8 +426,9 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
             return time_calls(torch, call, steps, 3, dist, sampler) / steps
 
         raw[f"n{n}_B{B}"] = {"n": n, "B": B, "t64": timed(rd.RD_ABA_FP64_UPDATE), "tdf": timed(0)}
-    # thread per instance against warp per instance (Sec. III-D scans) across
-    # batch sizes, double-float updates: microseconds [thread, warp, AUTO]
+    # the three mappings across batch sizes, double-float updates: microseconds
+    # [thread per instance, warp per instance (Sec. III-D scans), two warps per
+    # 32 instances, AUTO]
     xo = {}
     for n in (16, 64):
         model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
@@ -438,7 +439,8 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
             o = torch.empty_like(x[0])
             steps = max(3, min(K, 20))
             row = []
-            for fl in (rd.RD_ABA_THREAD_PER_INSTANCE, rd.RD_ABA_WARP_PER_INSTANCE, 0):
+            for fl in (rd.RD_ABA_THREAD_PER_INSTANCE, rd.RD_ABA_WARP_PER_INSTANCE,
+                       rd.RD_ABA_TWO_WARPS, 0):
                 t = time_calls(torch, lambda k: rd.aba(model, *x, workspace=ws, out=o, flags=fl),
                                steps, 3, dist, sampler)
                 row.append(t / steps * 1e6)

@@ -93,9 +93,17 @@ enum rd_status {
  * RD_ABA_JOINT_FRAMES or RD_ABA_SCANS_IN_DTYPE. */
 #define RD_ABA_WARP_PER_INSTANCE 0x20
 #define RD_ABA_THREAD_PER_INSTANCE 0x40
+/* aba_batch flag: two warps per 32 instances, one running the
+ * articulated-inertia recursion (Eq. abi, which depends on q only) and the other
+ * the bias sweeps, tau_hat, z_hat and c_hat beside it, then lambda and qdd
+ * (global constants, any n). Not combinable with the other mapping flags,
+ * RD_ABA_JOINT_FRAMES or RD_ABA_SCANS_IN_DTYPE. */
+#define RD_ABA_TWO_WARPS 0x80
 
-/* Per-instance status word of aba_batch (0 = fine). */
+/* Per-instance status word of aba_batch (0 = fine); bits. */
 #define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */
+#define RD_WARN_TIMEOUT 2  /* two-warp mapping: a bounded wait for the other warp gave up
+                              (about a second); that instance's qdd is invalid */
 
 /* Kernel variant for rnea_batch. */
 enum rd_variant {

@@ -415,6 +415,9 @@ RD_ABA_FP32_BIAS = 0x10
 RD_ABA_EXTENDED_BIAS_LINKS = 64
 RD_ABA_WARP_PER_INSTANCE = 0x20
 RD_ABA_THREAD_PER_INSTANCE = 0x40
+RD_ABA_TWO_WARPS = 0x80
+RD_WARN_SINGULAR = 1
+RD_WARN_TIMEOUT = 2
 
 
 def aba_workspace_bytes(model, B, dtype_code, flags=0):

@@ -186,7 +186,27 @@ bool aba_use_warp(int n, int B, int flags)
         return false;
     if (n < 48) return false;
     const bool fp64 = sizeof(T) == 8 || (flags & RD_ABA_FP64_UPDATE);
-    return B <= (fp64 ? 512 : 1024);
+    // against two warps per 32 instances (aba_use_pair), n = 64: warp 180 vs
+    // 201 us at B = 256, 226 vs 205 at 1024; n = 100 and 128: the warp wins up
+    // to B = 1024 (388 vs 434, 430 vs 563)
+    return B <= (fp64 || n < 96 ? 512 : 1024);
+}
+
+// Two warps per 32 instances: by flag, else for FP32 data where the measured
+// times favour it over one thread per instance (double-float updates, thread /
+// pair: n = 16: 1.25 at B = 1024, 1.04 at 16384, 0.80 at 65536; n = 64: 1.31 /
+// 1.17 / 0.76; n = 100: 1.90 / 1.20; FP64 updates: n = 64: 1.15 at 1024, 1.03 at
+// 16384, 1.05 at 65536; n = 100: 1.46 / 1.19) and the warp-per-instance mapping
+// does not apply.
+template <typename T>
+bool aba_use_pair(int n, int B, int flags)
+{
+    if (flags & RD_ABA_TWO_WARPS) return true;
+    if (sizeof(T) != 4 || (flags & (RD_ABA_THREAD_PER_INSTANCE | RD_ABA_WARP_PER_INSTANCE |
+                                    RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE)))
+        return false;
+    if (aba_use_warp<T>(n, B, flags)) return false;
+    return (flags & RD_ABA_FP64_UPDATE) ? true : B <= 16384;
 }
 
 template <typename T>
@@ -201,11 +221,22 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
         return rd_fail(RD_ERR_ARG, "aba_batch: needs a %zu-byte workspace (%zu given)", need,
                        ws_bytes);
     if (!aba_aligned16(ws)) return rd_fail(RD_ERR_ARG, "aba_batch: workspace not 16-byte aligned");
-    if ((flags & RD_ABA_WARP_PER_INSTANCE) &&
-        (flags & (RD_ABA_THREAD_PER_INSTANCE | RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE)))
-        return rd_fail(RD_ERR_ARG, "aba_batch: RD_ABA_WARP_PER_INSTANCE excludes "
-                                   "RD_ABA_THREAD_PER_INSTANCE, RD_ABA_JOINT_FRAMES and "
-                                   "RD_ABA_SCANS_IN_DTYPE");
+    {
+        const int maps = !!(flags & RD_ABA_WARP_PER_INSTANCE) + !!(flags & RD_ABA_TWO_WARPS) +
+                         !!(flags & RD_ABA_THREAD_PER_INSTANCE);
+        if (maps > 1 || ((flags & (RD_ABA_WARP_PER_INSTANCE | RD_ABA_TWO_WARPS)) &&
+                         (flags & (RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE))))
+            return rd_fail(RD_ERR_ARG, "aba_batch: RD_ABA_WARP_PER_INSTANCE, RD_ABA_TWO_WARPS and "
+                                       "RD_ABA_THREAD_PER_INSTANCE exclude one another, and the "
+                                       "first two RD_ABA_JOINT_FRAMES and RD_ABA_SCANS_IN_DTYPE");
+    }
+    if (aba_use_pair<T>(m->n, B, flags)) {
+        if constexpr (sizeof(T) == 4)
+            return rd_aba_pair_f32(m, B, q, qd, tau, qdd, status, ws, base18,
+                                   (flags & RD_ABA_FP64_UPDATE) != 0, ext, s);
+        else
+            return rd_aba_pair_f64(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    }
     if (aba_use_warp<T>(m->n, B, flags)) {
         if constexpr (sizeof(T) == 4)
             return rd_aba_warp_f32(m, B, q, qd, tau, qdd, status, base18,
