@@ -404,6 +404,12 @@ enum rd_schedule {
 /* Tuning word for RD_SCHED_PERSISTENT: threads per CTA = 2^t, CTAs per SM = c
  * (0 = library default: 128 threads, 4 CTAs per SM). */
 #define RD_FLEET_TUNE(log2_threads, ctas_per_sm) (((log2_threads) << 8) | (ctas_per_sm))
+/* OR-ed into the tune word of the persistent schedule: groups of 32 sorted
+ * requests that start with a forward-dynamics chain of at least min_links links
+ * (1..127) run two warps per 32 requests, one on the articulated-inertia
+ * recursion and one on the rest (as RD_ABA_TWO_WARPS); threads per block must
+ * then be a multiple of 64 up to 448. */
+#define RD_FLEET_TWO_WARPS(min_links) ((min_links) << 16)
 
 /*
  * rd_fleet_create -- upload nrobots chains (Sec. II-A model per robot).

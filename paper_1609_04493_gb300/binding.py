@@ -470,6 +470,10 @@ def RD_FLEET_TUNE(log2_threads, ctas_per_sm):
     return (int(log2_threads) << 8) | int(ctas_per_sm)
 
 
+def RD_FLEET_TWO_WARPS(min_links):
+    return int(min_links) << 16
+
+
 def _iptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 

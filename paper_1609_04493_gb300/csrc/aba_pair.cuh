@@ -24,31 +24,29 @@
 
 namespace rdyn {
 
-// Spin bound of warp Z's wait: 2^24 polls with a 64 ns pause, about a second.
-constexpr int kAbaPairSpinLimit = 1 << 24;
+// Spin bound of warp Z's wait: 2^22 polls with a 64 ns pause, a quarter of a
+// second or more. After one timeout a lane waits no more (its result is
+// flagged RD_WARN_TIMEOUT), so one instance never spins longer than that.
+constexpr int kAbaPairSpinLimit = 1 << 22;
 
+// One instance's share of the work for one of the two warps (role 0: J, role
+// 1: Z). The caller sets *progress to n or more (nothing published) and *jbad
+// to 0, and makes both visible to the pair, before either role starts. qr, qdr,
+// taur, qddr: the instance's rows; ws / wsz with (B, b): its workspace slots.
+// Role Z returns the status word, role J 0. The body synchronises with nothing
+// but its partner lane's progress counter: callers may run it on any subset of
+// a warp's lanes (fleets mix request kinds within a warp).
 template <typename T, typename D, typename TB, int TRIG>
-__global__ void __launch_bounds__(64)
-aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__restrict__ sdf,
-                int n, int B, const T *__restrict__ q, const T *__restrict__ qd,
-                const T *__restrict__ tau, T *__restrict__ qdd_out, int *__restrict__ status,
-                T *__restrict__ ws, D *__restrict__ wsz, BaseParams<T> base)
+__device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
+                                             const D *__restrict__ sd,
+                                             const DF *__restrict__ sdf, int n,
+                                             const T *__restrict__ qr, const T *__restrict__ qdr,
+                                             const T *__restrict__ taur, T *__restrict__ qddr,
+                                             T *__restrict__ ws, D *__restrict__ wsz, int B,
+                                             int b, const BaseParams<T> &base,
+                                             volatile int *progress, int *jbad)
 {
     constexpr bool kExt = !std::is_same<TB, T>::value;
-    __shared__ volatile int progress[32];
-    __shared__ int jbad[32];
-    const int role = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const int b0 = blockIdx.x * 32 + lane;
-    const bool live = b0 < B;
-    const int b = live ? b0 : B - 1;  // idle lanes recompute the last instance, write nothing
-    const size_t row = (size_t)b * (size_t)n;
-    const T *qr = q + row, *qdr = qd + row, *taur = tau + row;
-    if (role == 0) {
-        progress[lane] = n;
-        jbad[lane] = 0;
-    }
-    __syncthreads();
 
     // sin / cos of link i in the bias precision, as sweep 1 forms them
     auto trig_tb = [&](int i, TB &s, TB &c) {
@@ -99,17 +97,17 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
             const D Om = Jh.C.zz;
             if (!dpositive(Om)) bad = 1;
             invOm = drecip(Om);
-            if (live) {
+            {
                 const D vals[6] = {Uv[0], Uv[1], Uv[2], Uw[0], Uw[1], Uw[2]};
 #pragma unroll
                 for (int k = 0; k < 6; ++k) aba_zput(wsz, B, b, i, k, vals[k]);
                 aba_zput(wsz, B, b, i, 7, invOm);
             }
-            if (i == 0) jbad[lane] = bad;
+            if (i == 0) *jbad = bad;
             __threadfence_block();
-            progress[lane] = i;
+            *progress = i;
         }
-        return;
+        return 0;
     }
 
     // ---- warp Z. Sweep 1: bias motion (qdd = 0) and bias wrenches, base to tip
@@ -139,17 +137,14 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
             x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, __ldg(qdr + i), T(0), x);
             Fh = bias_wrench(L.m, L.c, L.I, x);
         }
-        if (live) {
+        {
             const TB vals[8] = {Fh.f.x, Fh.f.y, Fh.f.z, Fh.n.x, Fh.n.y, Fh.n.z, c, s};
 #pragma unroll
             for (int k = 0; k < 8; ++k) bias_put<TB>(ws, B, b, i, k, vals[k]);
         }
     }
 
-    // Sweep 2 (warp Z's part): wrench carry, tau_hat, c_hat, z_hat, tip to base.
-    // Idle lanes read the state of instance B - 1, which a live lane wrote:
-    // the warp barrier orders those writes before the reads.
-    __syncwarp();
+    // Sweep 2 (warp Z's part): wrench carry, tau_hat, c_hat, z_hat, tip to base
     int timeout = 0;
     Wrench<TB> F;
     F.f = mk3(dcvt<TB>(base.Fn[0]), dcvt<TB>(base.Fn[1]), dcvt<TB>(base.Fn[2]));
@@ -190,7 +185,7 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
         if constexpr (kExt) tau_hat = dcvt<D>(DF(__ldg(taur + i)) - F.n.z);
         else tau_hat = dsub_exact<D>(__ldg(taur + i), F.n.z);
         // U_i and 1 / Omega_i from warp J
-        for (int it = 0; progress[lane] > i; ++it) {
+        for (int it = 0; !timeout && *progress > i; ++it) {
             if (it >= kAbaPairSpinLimit) {
                 timeout = 1;
                 break;
@@ -202,7 +197,7 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
         for (int k = 0; k < 6; ++k) Up[k] = ldz(i, k);
         const D invOm = ldz(i, 7);
         chat_up = (tau_hat - z.n.z) * invOm;
-        if (live) aba_zput(wsz, B, b, i, 6, chat_up);
+        aba_zput(wsz, B, b, i, 6, chat_up);
         const D *ri = sd + i * kAbaDh64;
         if constexpr (kExt) {
             const DF *rf = sdf + i * kAbaDh64;
@@ -218,7 +213,7 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
     }
 
     // Sweep 3: lambda and qdd, base to tip
-    int bad = jbad[lane];
+    int bad = *jbad;
     V3<D> lv = mk3(D(0), D(0), D(0)), lw = mk3(D(0), D(0), D(0));
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
@@ -238,9 +233,34 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
         lv = av;
         lw = aw;
         if (disnan(qdd_i)) bad = 1;
-        if (live) qdd_out[row + i] = dcvt<T>(qdd_i);
+        qddr[i] = dcvt<T>(qdd_i);
     }
-    if (status && live) status[b] = (bad ? RD_WARN_SINGULAR : 0) | (timeout ? RD_WARN_TIMEOUT : 0);
+    return (bad ? RD_WARN_SINGULAR : 0) | (timeout ? RD_WARN_TIMEOUT : 0);
+}
+
+template <typename T, typename D, typename TB, int TRIG>
+__global__ void __launch_bounds__(64)
+aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__restrict__ sdf,
+                int n, int B, const T *__restrict__ q, const T *__restrict__ qd,
+                const T *__restrict__ tau, T *__restrict__ qdd_out, int *__restrict__ status,
+                T *__restrict__ ws, D *__restrict__ wsz, BaseParams<T> base)
+{
+    __shared__ volatile int progress[32];
+    __shared__ int jbad[32];
+    const int role = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 32 + lane;
+    if (role == 0) {
+        progress[lane] = n;
+        jbad[lane] = 0;
+    }
+    __syncthreads();
+    if (b >= B) return;  // both lanes of an idle instance; nothing waits on them
+    const size_t row = (size_t)b * (size_t)n;
+    const int st = aba_pair_role<T, D, TB, TRIG>(role, sc, sd, sdf, n, q + row, qd + row, tau + row,
+                                                 qdd_out + row, ws, wsz, B, b, base,
+                                                 &progress[lane], &jbad[lane]);
+    if (role == 1 && status) status[b] = st;
 }
 
 }  // namespace rdyn

@@ -23,7 +23,10 @@
 //   per-group:  one ordinary launch per run of equal (kind, n) in the sorted
 //               order -- the "one launch per request size" comparison.
 #pragma once
+#include <climits>
+
 #include "aba_dh.cuh"
+#include "aba_pair.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
@@ -51,6 +54,10 @@ struct FleetArgs {
     // double-float (FP32 data, chains beyond RD_ABA_EXTENDED_BIAS_LINKS)
     const DF *records_df;
     int ext_groups;
+    // two-warp forward dynamics (fleet_pair_kernel): the first pair_groups
+    // groups of 32 sorted requests, taken through pair_counter
+    int pair_groups;
+    int *pair_counter;
     int R;
     const T *q, *qd, *in2;    // in2: qdd (inverse) or tau (forward)
     T *out;                   // tau (inverse) or qdd (forward)
@@ -109,6 +116,34 @@ __device__ __forceinline__ void rnea_dh_instance(const T *__restrict__ sc, int n
     }
 }
 
+// Boundary terms in a robot's frames: V_0, dV_0 to D_{-1} (Ad_{G^-1}:
+// (R^T (v + w x p), R^T w)); F_{n+1} from frame n to D_{n-1}:
+// (R^T f, R^T (n - r x f)).
+template <typename T, typename D>
+__device__ __forceinline__ void fleet_base(const FleetArgs<T, D> &a, int robot, BaseParams<T> &bp)
+{
+    const T *g = a.robot_gb + (size_t)robot * 12;
+    const V3<T> p = mk3(g[9], g[10], g[11]);
+    const V3<T> v0 = mk3(a.base.V0[0], a.base.V0[1], a.base.V0[2]);
+    const V3<T> w0 = mk3(a.base.V0[3], a.base.V0[4], a.base.V0[5]);
+    const V3<T> a0 = mk3(a.base.dV0[0], a.base.dV0[1], a.base.dV0[2]);
+    const V3<T> al0 = mk3(a.base.dV0[3], a.base.dV0[4], a.base.dV0[5]);
+    const V3<T> vv = mulAT(g, cross_add(w0, p, v0)), ww = mulAT(g, w0);
+    const V3<T> aa = mulAT(g, cross_add(al0, p, a0)), al = mulAT(g, al0);
+    bp.V0[0] = vv.x; bp.V0[1] = vv.y; bp.V0[2] = vv.z;
+    bp.V0[3] = ww.x; bp.V0[4] = ww.y; bp.V0[5] = ww.z;
+    bp.dV0[0] = aa.x; bp.dV0[1] = aa.y; bp.dV0[2] = aa.z;
+    bp.dV0[3] = al.x; bp.dV0[4] = al.y; bp.dV0[5] = al.z;
+    const T *tn = a.robot_tn + (size_t)robot * 12;
+    const V3<T> f = mk3(a.base.Fn[0], a.base.Fn[1], a.base.Fn[2]);
+    const V3<T> nn = mk3(a.base.Fn[3], a.base.Fn[4], a.base.Fn[5]);
+    const V3<T> rr = mk3(tn[9], tn[10], tn[11]);
+    const V3<T> fp = mulAT(tn, f);
+    const V3<T> np = mulAT(tn, sub3(nn, cross3(rr, f)));
+    bp.Fn[0] = fp.x; bp.Fn[1] = fp.y; bp.Fn[2] = fp.z;
+    bp.Fn[3] = np.x; bp.Fn[4] = np.y; bp.Fn[5] = np.z;
+}
+
 // The request at sorted position k.
 template <typename T, typename D>
 __device__ __forceinline__ void fleet_request(const FleetArgs<T, D> &a, int k)
@@ -118,32 +153,8 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T, D> &a, int k)
     const int n = a.robot_n[robot];
     const long long lo = a.robot_link[robot];
     const long long off = a.req_off[r];
-    // boundary terms in this robot's frames: V_0, dV_0 to D_{-1} (Ad_{G^-1}:
-    // (R^T (v + w x p), R^T w)); F_{n+1} from frame n to D_{n-1}:
-    // (R^T f, R^T (n - r x f))
     BaseParams<T> bp;
-    {
-        const T *g = a.robot_gb + (size_t)robot * 12;
-        const V3<T> p = mk3(g[9], g[10], g[11]);
-        const V3<T> v0 = mk3(a.base.V0[0], a.base.V0[1], a.base.V0[2]);
-        const V3<T> w0 = mk3(a.base.V0[3], a.base.V0[4], a.base.V0[5]);
-        const V3<T> a0 = mk3(a.base.dV0[0], a.base.dV0[1], a.base.dV0[2]);
-        const V3<T> al0 = mk3(a.base.dV0[3], a.base.dV0[4], a.base.dV0[5]);
-        const V3<T> vv = mulAT(g, cross_add(w0, p, v0)), ww = mulAT(g, w0);
-        const V3<T> aa = mulAT(g, cross_add(al0, p, a0)), al = mulAT(g, al0);
-        bp.V0[0] = vv.x; bp.V0[1] = vv.y; bp.V0[2] = vv.z;
-        bp.V0[3] = ww.x; bp.V0[4] = ww.y; bp.V0[5] = ww.z;
-        bp.dV0[0] = aa.x; bp.dV0[1] = aa.y; bp.dV0[2] = aa.z;
-        bp.dV0[3] = al.x; bp.dV0[4] = al.y; bp.dV0[5] = al.z;
-        const T *tn = a.robot_tn + (size_t)robot * 12;
-        const V3<T> f = mk3(a.base.Fn[0], a.base.Fn[1], a.base.Fn[2]);
-        const V3<T> nn = mk3(a.base.Fn[3], a.base.Fn[4], a.base.Fn[5]);
-        const V3<T> rr = mk3(tn[9], tn[10], tn[11]);
-        const V3<T> fp = mulAT(tn, f);
-        const V3<T> np = mulAT(tn, sub3(nn, cross3(rr, f)));
-        bp.Fn[0] = fp.x; bp.Fn[1] = fp.y; bp.Fn[2] = fp.z;
-        bp.Fn[3] = np.x; bp.Fn[4] = np.y; bp.Fn[5] = np.z;
-    }
+    fleet_base(a, robot, bp);
     const T *sc = a.consts + lo * kDhConsts;
     if (a.req_kind[r] == 0) {
         rnea_dh_instance<T, kTrigPoly>(sc, n, a.q + off, a.qd + off, a.in2 + off, a.out + off, bp);
@@ -164,6 +175,94 @@ __device__ __forceinline__ void fleet_request(const FleetArgs<T, D> &a, int k)
                 sc, a.records + lo * kAbaDh64, n, a.q + off, a.qd + off, a.in2 + off,
                 a.out + off, wt, wz, 32, k & 31, bp);
         if (a.status) a.status[r] = bad ? 1 : 0;
+    }
+}
+
+// The request at sorted position k for one warp of a pair (role 0: the
+// articulated inertias; role 1: the rest of forward dynamics; aba_pair.cuh).
+// An inverse-dynamics request in a pair group runs on role 0 alone.
+template <typename T, typename D>
+__device__ __forceinline__ void fleet_request_pair(const FleetArgs<T, D> &a, int k, int role,
+                                                   volatile int *progress, int *jbad)
+{
+    const int r = a.order[k];
+    const int robot = a.req_robot[r];
+    const int n = a.robot_n[robot];
+    const long long lo = a.robot_link[robot];
+    const long long off = a.req_off[r];
+    if (a.req_kind[r] == 0) {
+        if (role == 0) fleet_request(a, k);
+        return;
+    }
+    BaseParams<T> bp;
+    fleet_base(a, robot, bp);
+    const T *sc = a.consts + lo * kDhConsts;
+    const int g = k >> 5;
+    T *wt = reinterpret_cast<T *>(a.ws + a.group_ws[g]);
+    D *wz = reinterpret_cast<D *>(a.ws + a.group_wz[g]);
+    int st = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (g < a.ext_groups)
+            st = aba_pair_role<T, D, DF, kTrigPoly>(role, sc, a.records + lo * kAbaDh64,
+                                                    a.records_df + lo * kAbaDh64, n, a.q + off,
+                                                    a.qd + off, a.in2 + off, a.out + off, wt, wz,
+                                                    32, k & 31, bp, progress, jbad);
+        else
+            st = aba_pair_role<T, D, T, kTrigPoly>(role, sc, a.records + lo * kAbaDh64,
+                                                   a.records_df + lo * kAbaDh64, n, a.q + off,
+                                                   a.qd + off, a.in2 + off, a.out + off, wt, wz, 32,
+                                                   k & 31, bp, progress, jbad);
+    } else {
+        st = aba_pair_role<T, D, T, kTrigPoly>(role, sc, a.records + lo * kAbaDh64, nullptr, n,
+                                               a.q + off, a.qd + off, a.in2 + off, a.out + off,
+                                               wt, wz, 32, k & 31, bp, progress, jbad);
+    }
+    if (role == 1 && a.status) a.status[r] = st ? 1 : 0;
+}
+
+__device__ __forceinline__ void pair_barrier(int id)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// Persistent with two-warp forward dynamics. Warps 2p and 2p + 1 of a block form
+// a pair: first the pairs take the leading a.pair_groups groups of 32 sorted
+// requests (forward dynamics with long chains, sorted first), both warps on the
+// same group through one atomicAdd and a named barrier per step; then every
+// warp takes 32 of the remaining requests at a time, as fleet_persistent_kernel.
+// At most 7 pairs per block (named barriers 1..14).
+template <typename T, typename D>
+__global__ void fleet_pair_kernel(FleetArgs<T, D> a)
+{
+    __shared__ volatile int prog[7][32];
+    __shared__ int jbad[7][32];
+    __shared__ volatile int grp[7];
+    const int pair = threadIdx.x >> 6;
+    const int role = (threadIdx.x >> 5) & 1;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (role == 0) {
+            if (lane == 0) grp[pair] = atomicAdd(a.pair_counter, 1);
+            prog[pair][lane] = INT_MAX;
+            jbad[pair][lane] = 0;
+        }
+        __syncwarp();
+        pair_barrier(1 + 2 * pair);
+        const int g = grp[pair];
+        if (g >= a.pair_groups) break;
+        const int k = 32 * g + lane;
+        if (k < a.R) fleet_request_pair(a, k, role, &prog[pair][lane], &jbad[pair][lane]);
+        __syncwarp();
+        pair_barrier(2 + 2 * pair);
+    }
+    const int base = 32 * a.pair_groups;
+    for (;;) {
+        int start = 0;
+        if (lane == 0) start = base + atomicAdd(a.counter, 32);
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (start >= a.R) break;
+        const int k = start + lane;
+        if (k < a.R) fleet_request(a, k);
     }
 }
 

@@ -42,6 +42,10 @@ struct rd_plan {
     // run the bias sweeps in double-float (FP32 plans; longest chain beyond
     // RD_ABA_EXTENDED_BIAS_LINKS)
     int ext_groups = 0;
+    // per group of 32 sorted positions: the longest forward-dynamics chain that
+    // starts it (0 when it starts with inverse dynamics), for the two-warp
+    // schedule's threshold
+    std::vector<int> group_fd_n;
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     int sms = 0;
@@ -202,12 +206,14 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
     // first, such groups form a prefix.
     const int groups32 = (R + 31) / 32;
     std::vector<long long> gws(groups32, 0), gwz(groups32, 0);
+    std::vector<int> group_fd_n(groups32, 0);
     size_t ws = 0;
     int ext_groups = 0;
     for (int g = 0; g < groups32; ++g) {
         size_t nmax = 0;
         for (int k = 32 * g; k < R && k < 32 * g + 32; ++k)
             if (kind[order[k]] == RD_REQ_FD) nmax = std::max(nmax, (size_t)f->n[robot[order[k]]]);
+        group_fd_n[g] = kind[order[32 * g]] == RD_REQ_FD ? (int)nmax : 0;
         if (!nmax) continue;
         const bool ext = dtype == RD_F32 && nmax > RD_ABA_EXTENDED_BIAS_LINKS;
         if (ext) ext_groups = g + 1;
@@ -237,10 +243,11 @@ extern "C" int rd_plan_create(const rd_fleet *f, int R, const int *robot, const 
     if (e == cudaSuccess) e = upload(&p->req_off, off.data(), off.size());
     if (e == cudaSuccess) e = upload(&p->group_ws, gws.data(), gws.size());
     if (e == cudaSuccess) e = upload(&p->group_wz, gwz.data(), gwz.size());
-    if (e == cudaSuccess) e = cudaMalloc(&p->counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->counter, 2 * sizeof(int));  // + the pair counter
     if (e == cudaSuccess) e = cudaMalloc(&p->ws, std::max<size_t>(ws, 16));
     p->ws_bytes = ws;
     p->ext_groups = ext_groups;
+    p->group_fd_n = group_fd_n;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     for (int k = 0; k < rd_plan::kSide && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
@@ -267,9 +274,11 @@ extern "C" int rd_plan_groups(const rd_plan *p) { return p ? (int)p->groups.size
 
 namespace {
 
+// pair_n > 0: forward-dynamics groups whose first chain has at least pair_n
+// links run two warps per 32 requests (fleet_pair_kernel)
 template <typename T, typename D>
 int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, void *out,
-              const double *b18, int *status, int schedule, int tune, cudaStream_t s)
+              const double *b18, int *status, int schedule, int tune, int pair_n, cudaStream_t s)
 {
     const rd_fleet *f = p->fleet;
     rdyn::FleetArgs<T, D> a;
@@ -286,6 +295,8 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
     else a.records = f->abadf;
     a.records_df = f->abadf;
     a.ext_groups = p->ext_groups;
+    a.pair_groups = 0;
+    a.pair_counter = p->counter + 1;
     a.robot_n = f->robot_n;
     a.robot_link = f->robot_link;
     a.order = p->order;
@@ -308,7 +319,21 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
         a.base.Fn[k] = (T)b18[12 + k];
     }
     cudaError_t e = cudaSuccess;
-    if (schedule == RD_SCHED_PERSISTENT) {
+    if (schedule == RD_SCHED_PERSISTENT && pair_n > 0) {
+        // two-warp forward dynamics for the leading groups whose first request
+        // is a forward-dynamics chain of at least pair_n links
+        int pg = 0;
+        while (pg < (int)p->group_fd_n.size() && p->group_fd_n[pg] >= pair_n) ++pg;
+        a.pair_groups = pg;
+        int threads = (tune >> 8) & 0xff ? 1 << ((tune >> 8) & 0xff) : 128;
+        int per_sm = tune & 0xff ? tune & 0xff : 4;
+        if (threads < 64 || threads > 448 || threads % 64)
+            return rd_fail(RD_ERR_ARG, "fleet_batch: the two-warp schedule takes 64..448 threads "
+                                       "per block in multiples of 64 (%d)", threads);
+        e = cudaMemsetAsync(p->counter, 0, 2 * sizeof(int), s);
+        if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch: counter reset");
+        rdyn::fleet_pair_kernel<T, D><<<p->sms * per_sm, threads, 0, s>>>(a);
+    } else if (schedule == RD_SCHED_PERSISTENT) {
         int threads = (tune >> 8) & 0xff ? 1 << ((tune >> 8) & 0xff) : 128;
         int per_sm = tune & 0xff ? tune & 0xff : 4;
         if (threads < 32 || threads > 1024)
@@ -358,10 +383,14 @@ extern "C" int fleet_batch(const rd_plan *p, const void *q, const void *qd, cons
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool fp64_update = (schedule & RD_FLEET_FP64_UPDATE) != 0;
     schedule &= ~RD_FLEET_FP64_UPDATE;
+    const int pair_n = (tune >> 16) & 0xff;
+    if (pair_n && schedule != RD_SCHED_PERSISTENT)
+        return rd_fail(RD_ERR_ARG, "fleet_batch: two-warp forward dynamics needs the persistent "
+                                   "schedule");
     if (p->dtype == RD_F32) {
         if (fp64_update)
-            return run_fleet<float, double>(p, q, qd, in2, out, b18, status, schedule, tune, s);
-        return run_fleet<float, rdyn::DF>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+            return run_fleet<float, double>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n, s);
+        return run_fleet<float, rdyn::DF>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n, s);
     }
-    return run_fleet<double, double>(p, q, qd, in2, out, b18, status, schedule, tune, s);
+    return run_fleet<double, double>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n, s);
 }

@@ -156,8 +156,9 @@ def _stratified(kinds, lengths, per_group, seed=0):
 def test_fleet_uneven_workload_at_full_size(cuda_lib):
     """The bench's uneven workload exactly (100000 requests from seed 1609,
     its inputs, FP32): the persistent launch with FP64 inertia updates and
-    solves, one launch per (kind, n) group with the same, and the persistent
-    launch with the double-float default. 11 requests of every (kind, n) pair,
+    solves, one launch per (kind, n) group with the same, the persistent launch
+    with the double-float default, and both precisions with two warps per 32
+    forward-dynamics requests from 33 links. 11 requests of every (kind, n) pair,
     n = 6..100 (2090 requests), checked against the oracle on the FP32 bars."""
     import torch
 
@@ -180,12 +181,55 @@ def test_fleet_uneven_workload_at_full_size(cuda_lib):
         fn = oracle.rnea if kinds[r] == 0 else oracle.fd_aba
         refs[r] = fn(reqs[r]["chain"], h64[0][sl][None], h64[1][sl][None], h64[2][sl][None])
     f64 = rd.RD_FLEET_FP64_UPDATE
-    for schedule in (0 | f64, rd.RD_SCHED_PER_GROUP | f64, 0):
-        out = rd.fleet_batch(plan, *x, schedule=schedule).cpu().numpy().astype(np.float64)
+    pair = rd.RD_FLEET_TUNE(7, 2) | rd.RD_FLEET_TWO_WARPS(33)
+    for schedule, tune in ((0 | f64, 0), (rd.RD_SCHED_PER_GROUP | f64, 0), (0, 0), (0 | f64, pair),
+                           (0, pair)):
+        out = rd.fleet_batch(plan, *x, schedule=schedule, tune=tune).cpu().numpy().astype(np.float64)
         worst = {0: 0.0, 1: 0.0}
         for r in sample:
             o, n = plan.offsets[r], plan.lengths[r]
             e = oracle.rel_err(out[o:o + n][None], refs[r])
             worst[int(kinds[r])] = max(worst[int(kinds[r])], e)
-        assert worst[0] <= TOL_ID["float32"], (schedule, worst)
-        assert worst[1] <= TOL_FD["float32"], (schedule, worst)
+        assert worst[0] <= TOL_ID["float32"], (schedule, tune, worst)
+        assert worst[1] <= TOL_FD["float32"], (schedule, tune, worst)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+@pytest.mark.parametrize("min_links", [1, 33, 65])
+def test_fleet_two_warp_forward_dynamics(cuda_lib, dtype, min_links):
+    """RD_FLEET_TWO_WARPS: forward-dynamics groups from a length on run two warps
+    per 32 requests; every request against the oracle, and against the
+    one-thread-per-request schedule (FP64 to rounding, FP32 to a few ulps)."""
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 700, 2, 100, dtype, seed=31,
+                                                fd_fraction=0.4)
+    tune = cuda_lib.RD_FLEET_TUNE(7, 2) | cuda_lib.RD_FLEET_TWO_WARPS(min_links)
+    out = cuda_lib.fleet_batch(plan, *dev, tune=tune).cpu().numpy().astype(np.float64)
+    check(reqs, plan, kinds, host, out, dtype)
+    ref = cuda_lib.fleet_batch(plan, *dev).cpu().numpy().astype(np.float64)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(out - ref)) <= (1e-10 if dtype == "float64" else 1e-5) * scale
+
+
+def test_fleet_two_warps_fp64_update_and_status(cuda_lib):
+    import torch
+
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 300, 40, 100, "float32", seed=33,
+                                                fd_fraction=0.5)
+    status = torch.full((300,), -1, dtype=torch.int32, device="cuda")
+    tune = cuda_lib.RD_FLEET_TUNE(6, 4) | cuda_lib.RD_FLEET_TWO_WARPS(6)
+    out = cuda_lib.fleet_batch(plan, *dev, status=status, tune=tune,
+                               schedule=cuda_lib.RD_FLEET_FP64_UPDATE)
+    check(reqs, plan, kinds, host, out.cpu().numpy().astype(np.float64), "float32")
+    st = status.cpu().numpy()
+    assert np.all(st[kinds == 1] == 0)
+
+
+def test_fleet_two_warps_rejects_bad_shapes(cuda_lib):
+    reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 50, 4, 20, "float32", seed=35)
+    for tune in (cuda_lib.RD_FLEET_TUNE(5, 1) | cuda_lib.RD_FLEET_TWO_WARPS(6),
+                 cuda_lib.RD_FLEET_TUNE(9, 1) | cuda_lib.RD_FLEET_TWO_WARPS(6)):
+        with pytest.raises(cuda_lib.RdError):
+            cuda_lib.fleet_batch(plan, *dev, tune=tune)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.fleet_batch(plan, *dev, schedule=cuda_lib.RD_SCHED_PER_GROUP,
+                             tune=cuda_lib.RD_FLEET_TWO_WARPS(6))
