@@ -132,6 +132,12 @@ def rnd(x, digits=4):
     return x
 
 
+def short_us(t):
+    """Three significant digits; whole numbers from 100 on (a shorter line)."""
+    v = float(f"{t:.3g}")
+    return int(v) if v >= 100 else v
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -143,7 +149,7 @@ def parse_args():
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
     p.add_argument("--kernel-only",
                    choices=["f32", "f64", "f64df", "host", "vjp", "vjplane", "aba", "aba64",
-                            "abawarp", "fleet"],
+                            "abawarp", "abapair", "abatri", "fleet"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
@@ -151,7 +157,8 @@ def parse_args():
                         "size; vjp: adjoint n=32 B=8192; vjplane: adjoint n=32 B=4096, 8 lanes "
                         "per instance; aba: forward dynamics n=64 B=16384 (double-float updates; "
                         "aba64: FP64 updates); abawarp: forward dynamics n=64 B=1024, one warp per "
-                        "instance; fleet: 20000 mixed requests)")
+                        "instance; abapair / abatri: forward dynamics n=64 B=16384, two / three "
+                        "warps per 32 instances; fleet: 20000 mixed requests)")
     return p.parse_args()
 
 
@@ -393,8 +400,7 @@ def adjoint_report(raw, pk):
     out = {}
     for name, r in raw.items():
         fpl = VJP_FLOP_PER_LINK[1]
-        out[name] = {"us": r["t"] * 1e6, "value": r["B"] / r["t"],
-                     "frac": r["B"] * N_LINKS * fpl / r["t"] / pk.f32}
+        out[name] = {"us": r["t"] * 1e6, "frac": r["B"] * N_LINKS * fpl / r["t"] / pk.f32}
         for k, t in r.get("alt", {}).items():
             out[name][k] = t * 1e6
     out["flop_per_link"] = VJP_FLOP_PER_LINK[1]
@@ -426,25 +432,28 @@ def fd_section(torch, rd, chaingen, dev, dist, sampler, K):
             return time_calls(torch, call, steps, 3, dist, sampler) / steps
 
         raw[f"n{n}_B{B}"] = {"n": n, "B": B, "t64": timed(rd.RD_ABA_FP64_UPDATE), "tdf": timed(0)}
-    # the three mappings across batch sizes, double-float updates: microseconds
-    # [thread per instance, warp per instance (Sec. III-D scans), two warps per
-    # 32 instances, AUTO]
+    # the four mappings across batch sizes: microseconds [thread per instance,
+    # warp per instance (Sec. III-D scans), two warps per 32 instances, three
+    # warps per 32 instances, AUTO]; double-float updates at n = 16 and 64, FP64
+    # updates ("f64u") at n = 64
     xo = {}
-    for n in (16, 64):
+    cases = [(n, Bx, 0) for n in (16, 64) for Bx in (256, 1024, 4096, 16384)]
+    cases += [(64, Bx, rd.RD_ABA_FP64_UPDATE) for Bx in (256, 1024, 4096)]
+    for n, Bx, prec in cases:
         model = rd.Model(chaingen.make_chain(n, seed=chaingen.BASE_SEED))
-        for Bx in (256, 1024, 4096, 16384):
-            st = chaingen.make_states(Bx, n, seed=6100, kinds=("q", "qd", "tau"))
-            x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
-            ws = torch.empty(rd.aba_workspace_bytes(model, Bx, 0), dtype=torch.uint8, device=dev)
-            o = torch.empty_like(x[0])
-            steps = max(3, min(K, 20))
-            row = []
-            for fl in (rd.RD_ABA_THREAD_PER_INSTANCE, rd.RD_ABA_WARP_PER_INSTANCE,
-                       rd.RD_ABA_TWO_WARPS, 0):
-                t = time_calls(torch, lambda k: rd.aba(model, *x, workspace=ws, out=o, flags=fl),
-                               steps, 3, dist, sampler)
-                row.append(t / steps * 1e6)
-            xo[f"n{n}_B{Bx}"] = [float(f"{t:.3g}") for t in row]
+        st = chaingen.make_states(Bx, n, seed=6100, kinds=("q", "qd", "tau"))
+        x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
+        ws = torch.empty(rd.aba_workspace_bytes(model, Bx, 0, prec), dtype=torch.uint8,
+                         device=dev)
+        o = torch.empty_like(x[0])
+        steps = max(3, min(K, 20))
+        row = []
+        for fl in (rd.RD_ABA_THREAD_PER_INSTANCE, rd.RD_ABA_WARP_PER_INSTANCE,
+                   rd.RD_ABA_TWO_WARPS, rd.RD_ABA_THREE_WARPS, 0):
+            t = time_calls(torch, lambda k: rd.aba(model, *x, workspace=ws, out=o, flags=fl | prec),
+                           steps, 3, dist, sampler)
+            row.append(t / steps * 1e6)
+        xo[f"{'f64u_' if prec else ''}n{n}_B{Bx}"] = [short_us(t) for t in row]
     raw["crossover_us"] = xo
     return raw
 
@@ -463,7 +472,7 @@ def fd_report(raw, pk):
         t_exec = nb * (FD_EXEC_FLOP32_PER_LINK / pk.f32 + FD_EXEC_FLOP64_PER_LINK / pk.f64)
         t_alg = nb * (FD_FLOP32_PER_LINK / pk.f32 + FD_FLOP64_PER_LINK / pk.f64)
         t_df = nb * FD_DF_EXEC_FP32_INST_PER_LINK / pk.i32
-        out[name] = {"us": r["t64"] * 1e6, "value": r["B"] / r["t64"], "frac": t_exec / r["t64"],
+        out[name] = {"us": r["t64"] * 1e6, "frac": t_exec / r["t64"],
                      "frac_alg": t_alg / r["t64"], "df_us": r["tdf"] * 1e6,
                      "df_frac": t_df / r["tdf"]}
     return out
@@ -568,7 +577,6 @@ def uneven_report(raw, pk):
         r = raw[name]
         floor = t_id + (t_df if name == "df_persistent" else t_fd)
         out[name] = {"us": r["t"] * 1e6, "value": raw["count"] / r["t"], "frac": floor / r["t"]}
-    out["launches_per_group"] = raw["groups"]
     return out
 
 
@@ -841,10 +849,12 @@ def run_kernel_only(args):
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]
         for _ in range(calls):
             res = rd.rnea_vjp(model, *x, mode=mode)[0]
-    elif args.kernel_only in ("aba", "aba64", "abawarp"):
+    elif args.kernel_only in ("aba", "aba64", "abawarp", "abapair", "abatri"):
         flags = {"aba": rd.RD_ABA_THREAD_PER_INSTANCE,
                  "aba64": rd.RD_ABA_FP64_UPDATE | rd.RD_ABA_THREAD_PER_INSTANCE,
-                 "abawarp": rd.RD_ABA_WARP_PER_INSTANCE}[args.kernel_only]
+                 "abawarp": rd.RD_ABA_WARP_PER_INSTANCE,
+                 "abapair": rd.RD_ABA_TWO_WARPS,
+                 "abatri": rd.RD_ABA_THREE_WARPS}[args.kernel_only]
         Ba = 1024 if args.kernel_only == "abawarp" else 16384
         model = rd.Model(chaingen.make_chain(64, seed=chaingen.BASE_SEED))
         st = chaingen.make_states(Ba, 64, seed=6000, kinds=("q", "qd", "tau"))

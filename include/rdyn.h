@@ -99,6 +99,12 @@ enum rd_status {
  * (global constants, any n). Not combinable with the other mapping flags,
  * RD_ABA_JOINT_FRAMES or RD_ABA_SCANS_IN_DTYPE. */
 #define RD_ABA_TWO_WARPS 0x80
+/* aba_batch flag: as RD_ABA_TWO_WARPS with the articulated-inertia recursion
+ * itself split over two warps by block of the 6x6 inertia (one the
+ * translational and rotational diagonal blocks, the other the off-diagonal
+ * block, exchanging their shift terms per link), three warps per 32 instances.
+ * Same results to rounding; same exclusions. */
+#define RD_ABA_THREE_WARPS 0x100
 
 /* Per-instance status word of aba_batch (0 = fine); bits. */
 #define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */

@@ -416,6 +416,7 @@ RD_ABA_EXTENDED_BIAS_LINKS = 64
 RD_ABA_WARP_PER_INSTANCE = 0x20
 RD_ABA_THREAD_PER_INSTANCE = 0x40
 RD_ABA_TWO_WARPS = 0x80
+RD_ABA_THREE_WARPS = 0x100
 RD_WARN_SINGULAR = 1
 RD_WARN_TIMEOUT = 2
 

@@ -203,10 +203,34 @@ bool aba_use_pair(int n, int B, int flags)
 {
     if (flags & RD_ABA_TWO_WARPS) return true;
     if (sizeof(T) != 4 || (flags & (RD_ABA_THREAD_PER_INSTANCE | RD_ABA_WARP_PER_INSTANCE |
-                                    RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE)))
+                                    RD_ABA_THREE_WARPS | RD_ABA_JOINT_FRAMES |
+                                    RD_ABA_SCANS_IN_DTYPE)))
         return false;
     if (aba_use_warp<T>(n, B, flags)) return false;
     return (flags & RD_ABA_FP64_UPDATE) ? true : B <= 16384;
+}
+
+// Three warps per 32 instances (aba_tri.cuh): by flag, else for FP32 data where
+// the measured times favour it (GB300, CUDA events, two-warp /
+// three-warp time): double-float updates, n = 16: 1.27 at B = 1024, 1.01 at
+// 4096, 0.99 at 16384; n = 32: 1.23 / 0.99 / 0.99; n = 64: 1.22 at B = 256 and
+// 1024, 0.98 / 0.96 (and 161 us against 180 for one warp per instance at n = 64,
+// B = 256); with the double-float bias sweeps beyond 64 links the split does not
+// pay (n = 100: 0.99 at 1024, 0.82 at 4096). FP64 updates: 1.21 to 1.31 up to B =
+// 4096 for n = 16 to 100, 0.92 to 0.97 at 16384; below B = 512 one warp per
+// instance stays ahead for n >= 48. Beyond the crossover every instance is
+// resident at once and the kernels stall on instruction fetch; the third warp
+// then adds work without shortening the chain.
+template <typename T>
+bool aba_use_tri(int n, int B, int flags, bool ext)
+{
+    if (flags & RD_ABA_THREE_WARPS) return true;
+    if (sizeof(T) != 4 ||
+        (flags & (RD_ABA_THREAD_PER_INSTANCE | RD_ABA_WARP_PER_INSTANCE | RD_ABA_TWO_WARPS |
+                  RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE)))
+        return false;
+    if (flags & RD_ABA_FP64_UPDATE) return B <= 4096 && !aba_use_warp<T>(n, B, flags);
+    return !ext && B <= 2048;
 }
 
 template <typename T>
@@ -223,12 +247,21 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
     if (!aba_aligned16(ws)) return rd_fail(RD_ERR_ARG, "aba_batch: workspace not 16-byte aligned");
     {
         const int maps = !!(flags & RD_ABA_WARP_PER_INSTANCE) + !!(flags & RD_ABA_TWO_WARPS) +
-                         !!(flags & RD_ABA_THREAD_PER_INSTANCE);
-        if (maps > 1 || ((flags & (RD_ABA_WARP_PER_INSTANCE | RD_ABA_TWO_WARPS)) &&
-                         (flags & (RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE))))
-            return rd_fail(RD_ERR_ARG, "aba_batch: RD_ABA_WARP_PER_INSTANCE, RD_ABA_TWO_WARPS and "
-                                       "RD_ABA_THREAD_PER_INSTANCE exclude one another, and the "
-                                       "first two RD_ABA_JOINT_FRAMES and RD_ABA_SCANS_IN_DTYPE");
+                         !!(flags & RD_ABA_THREE_WARPS) + !!(flags & RD_ABA_THREAD_PER_INSTANCE);
+        if (maps > 1 ||
+            ((flags & (RD_ABA_WARP_PER_INSTANCE | RD_ABA_TWO_WARPS | RD_ABA_THREE_WARPS)) &&
+             (flags & (RD_ABA_JOINT_FRAMES | RD_ABA_SCANS_IN_DTYPE))))
+            return rd_fail(RD_ERR_ARG, "aba_batch: RD_ABA_WARP_PER_INSTANCE, RD_ABA_TWO_WARPS, "
+                                       "RD_ABA_THREE_WARPS and RD_ABA_THREAD_PER_INSTANCE exclude "
+                                       "one another, and the first three RD_ABA_JOINT_FRAMES and "
+                                       "RD_ABA_SCANS_IN_DTYPE");
+    }
+    if (aba_use_tri<T>(m->n, B, flags, ext)) {
+        if constexpr (sizeof(T) == 4)
+            return rd_aba_tri_f32(m, B, q, qd, tau, qdd, status, ws, base18,
+                                  (flags & RD_ABA_FP64_UPDATE) != 0, ext, s);
+        else
+            return rd_aba_tri_f64(m, B, q, qd, tau, qdd, status, ws, base18, s);
     }
     if (aba_use_pair<T>(m->n, B, flags)) {
         if constexpr (sizeof(T) == 4)

@@ -29,86 +29,114 @@ namespace rdyn {
 // flagged RD_WARN_TIMEOUT), so one instance never spins longer than that.
 constexpr int kAbaPairSpinLimit = 1 << 22;
 
-// One instance's share of the work for one of the two warps (role 0: J, role
-// 1: Z). The caller sets *progress to n or more (nothing published) and *jbad
-// to 0, and makes both visible to the pair, before either role starts. qr, qdr,
-// taur, qddr: the instance's rows; ws / wsz with (B, b): its workspace slots.
-// Role Z returns the status word, role J 0. The body synchronises with nothing
-// but its partner lane's progress counter: callers may run it on any subset of
-// a warp's lanes (fleets mix request kinds within a warp).
+// Bounded wait of one lane until both counters have reached link i or below
+// (pu == pv for a single producer), then the fence that orders the producer's
+// stores before this lane's loads. After one timeout a lane waits no more.
+__device__ __forceinline__ void aba_wait2(const volatile int *pu, const volatile int *pv, int i,
+                                          int &timeout)
+{
+    for (int it = 0; !timeout && (*pu > i || *pv > i); ++it) {
+        if (it >= kAbaPairSpinLimit) {
+            timeout = 1;
+            break;
+        }
+        __nanosleep(64);
+    }
+    __threadfence_block();
+}
+
+// sin / cos of link i in the bias precision TB, as sweep 1 forms them
+template <typename T, typename TB, int TRIG>
+__device__ __forceinline__ void aba_trig_tb(const T *__restrict__ sc, const DF *__restrict__ sdf,
+                                            const T *__restrict__ qr, int i, TB &s, TB &c)
+{
+    if constexpr (!std::is_same<TB, T>::value)
+        df_sincos((double)__ldg(qr + i) + df_to_double(sdf[i * kAbaDh64 + 5]), &s, &c);
+    else
+        dh_trig<T, TRIG>(__ldg(qr + i) + sc[i * kDhConsts + 5], &s, &c);
+}
+
+// Warp J's share of one instance: the articulated inertias, tip to base; U_i
+// and 1 / Omega_i into the workspace slots (wsz, B, b), then *progress = i.
+// *jbad: 1 if some Omega_i was not positive, written before the last
+// publication.
 template <typename T, typename D, typename TB, int TRIG>
-__device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
-                                             const D *__restrict__ sd,
-                                             const DF *__restrict__ sdf, int n,
-                                             const T *__restrict__ qr, const T *__restrict__ qdr,
-                                             const T *__restrict__ taur, T *__restrict__ qddr,
-                                             T *__restrict__ ws, D *__restrict__ wsz, int B,
-                                             int b, const BaseParams<T> &base,
-                                             volatile int *progress, int *jbad)
+__device__ __forceinline__ void aba_pair_j(const T *__restrict__ sc, const D *__restrict__ sd,
+                                           const DF *__restrict__ sdf, int n,
+                                           const T *__restrict__ qr, D *__restrict__ wsz, int B,
+                                           int b, volatile int *progress, int *jbad)
+{
+    auto trig_tb = [&](int i, TB &s, TB &c) { aba_trig_tb<T, TB, TRIG>(sc, sdf, qr, i, s, c); };
+    // ---- warp J: the articulated inertias, tip to base
+    int bad = 0;
+    AbiT<D> Jh;
+    D Uv[3], Uw[3], invOm = D(0);
+#pragma unroll 1
+    for (int i = n - 1; i >= 0; --i) {
+        const D *ri = sd + i * kAbaDh64;
+        if (i > 0) {
+            prefetch_l1(sd + (i - 1) * kAbaDh64);
+            prefetch_l1(sd + (i - 1) * kAbaDh64 + kAbaDh64 / 2);
+        }
+        if (i == n - 1) {
+            const D m = ri[6], zero = D(0);
+            Jh.A = Sym3<D>{m, m, m, zero, zero, zero};
+            Jh.Bm[0] = zero;    Jh.Bm[1] = ri[18];  Jh.Bm[2] = -ri[17];
+            Jh.Bm[3] = -ri[18]; Jh.Bm[4] = zero;    Jh.Bm[5] = ri[16];
+            Jh.Bm[6] = ri[17];  Jh.Bm[7] = -ri[16]; Jh.Bm[8] = zero;
+            Jh.C = Sym3<D>{ri[19], ri[20], ri[21], ri[22], ri[23], ri[24]};
+        } else {
+            AbiT<D> P;
+            const D ux = Uv[0] * invOm, uy = Uv[1] * invOm, uz = Uv[2] * invOm;
+            const D wx = Uw[0] * invOm, wy = Uw[1] * invOm;
+            P.A = Sym3<D>{fma(-ux, Uv[0], Jh.A.xx), fma(-uy, Uv[1], Jh.A.yy),
+                          fma(-uz, Uv[2], Jh.A.zz), fma(-ux, Uv[1], Jh.A.xy),
+                          fma(-ux, Uv[2], Jh.A.xz), fma(-uy, Uv[2], Jh.A.yz)};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                P.Bm[3 * r] = fma(-Uv[r], wx, Jh.Bm[3 * r]);
+                P.Bm[3 * r + 1] = fma(-Uv[r], wy, Jh.Bm[3 * r + 1]);
+                P.Bm[3 * r + 2] = D(0);
+            }
+            P.C = Sym3<D>{fma(-wx, Uw[0], Jh.C.xx), fma(-wy, Uw[1], Jh.C.yy), D(0),
+                          fma(-wx, Uw[1], Jh.C.xy), D(0), D(0)};
+            TB s1, c1;
+            trig_tb(i + 1, s1, c1);
+            Jh = aba_dh_update(P, dcvt<D>(c1), dcvt<D>(s1), sd + (i + 1) * kAbaDh64, ri);
+        }
+        Uv[0] = Jh.Bm[2]; Uv[1] = Jh.Bm[5]; Uv[2] = Jh.Bm[8];
+        Uw[0] = Jh.C.xz;  Uw[1] = Jh.C.yz;  Uw[2] = Jh.C.zz;
+        const D Om = Jh.C.zz;
+        if (!dpositive(Om)) bad = 1;
+        invOm = drecip(Om);
+        {
+            const D vals[6] = {Uv[0], Uv[1], Uv[2], Uw[0], Uw[1], Uw[2]};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) aba_zput(wsz, B, b, i, k, vals[k]);
+            aba_zput(wsz, B, b, i, 7, invOm);
+        }
+        if (i == 0) *jbad = bad;
+        __threadfence_block();
+        *progress = i;
+    }
+}
+
+// Warp Z's share of one instance: sweep 1, then sweep 2's wrench carry and
+// z_hat / c_hat as U_i and 1 / Omega_i arrive (both counters pu, pv at i or
+// below), then sweep 3. jbu, jbv: the producers' flag words (bit 0: a
+// non-positive Omega_i, bit 1: a producer timed out). Returns the status word.
+template <typename T, typename D, typename TB, int TRIG>
+__device__ __forceinline__ int aba_pair_z(const T *__restrict__ sc, const D *__restrict__ sd,
+                                          const DF *__restrict__ sdf, int n,
+                                          const T *__restrict__ qr, const T *__restrict__ qdr,
+                                          const T *__restrict__ taur, T *__restrict__ qddr,
+                                          T *__restrict__ ws, D *__restrict__ wsz, int B, int b,
+                                          const BaseParams<T> &base, const volatile int *pu,
+                                          const volatile int *pv, const int *jbu, const int *jbv)
 {
     constexpr bool kExt = !std::is_same<TB, T>::value;
+    auto trig_tb = [&](int i, TB &s, TB &c) { aba_trig_tb<T, TB, TRIG>(sc, sdf, qr, i, s, c); };
 
-    // sin / cos of link i in the bias precision, as sweep 1 forms them
-    auto trig_tb = [&](int i, TB &s, TB &c) {
-        if constexpr (kExt) df_sincos((double)__ldg(qr + i) + df_to_double(sdf[i * kAbaDh64 + 5]), &s, &c);
-        else dh_trig<T, TRIG>(__ldg(qr + i) + sc[i * kDhConsts + 5], &s, &c);
-    };
-
-    if (role == 0) {
-        // ---- warp J: the articulated inertias, tip to base
-        int bad = 0;
-        AbiT<D> Jh;
-        D Uv[3], Uw[3], invOm = D(0);
-#pragma unroll 1
-        for (int i = n - 1; i >= 0; --i) {
-            const D *ri = sd + i * kAbaDh64;
-            if (i > 0) {
-                prefetch_l1(sd + (i - 1) * kAbaDh64);
-                prefetch_l1(sd + (i - 1) * kAbaDh64 + kAbaDh64 / 2);
-            }
-            if (i == n - 1) {
-                const D m = ri[6], zero = D(0);
-                Jh.A = Sym3<D>{m, m, m, zero, zero, zero};
-                Jh.Bm[0] = zero;    Jh.Bm[1] = ri[18];  Jh.Bm[2] = -ri[17];
-                Jh.Bm[3] = -ri[18]; Jh.Bm[4] = zero;    Jh.Bm[5] = ri[16];
-                Jh.Bm[6] = ri[17];  Jh.Bm[7] = -ri[16]; Jh.Bm[8] = zero;
-                Jh.C = Sym3<D>{ri[19], ri[20], ri[21], ri[22], ri[23], ri[24]};
-            } else {
-                AbiT<D> P;
-                const D ux = Uv[0] * invOm, uy = Uv[1] * invOm, uz = Uv[2] * invOm;
-                const D wx = Uw[0] * invOm, wy = Uw[1] * invOm;
-                P.A = Sym3<D>{fma(-ux, Uv[0], Jh.A.xx), fma(-uy, Uv[1], Jh.A.yy),
-                              fma(-uz, Uv[2], Jh.A.zz), fma(-ux, Uv[1], Jh.A.xy),
-                              fma(-ux, Uv[2], Jh.A.xz), fma(-uy, Uv[2], Jh.A.yz)};
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    P.Bm[3 * r] = fma(-Uv[r], wx, Jh.Bm[3 * r]);
-                    P.Bm[3 * r + 1] = fma(-Uv[r], wy, Jh.Bm[3 * r + 1]);
-                    P.Bm[3 * r + 2] = D(0);
-                }
-                P.C = Sym3<D>{fma(-wx, Uw[0], Jh.C.xx), fma(-wy, Uw[1], Jh.C.yy), D(0),
-                              fma(-wx, Uw[1], Jh.C.xy), D(0), D(0)};
-                TB s1, c1;
-                trig_tb(i + 1, s1, c1);
-                Jh = aba_dh_update(P, dcvt<D>(c1), dcvt<D>(s1), sd + (i + 1) * kAbaDh64, ri);
-            }
-            Uv[0] = Jh.Bm[2]; Uv[1] = Jh.Bm[5]; Uv[2] = Jh.Bm[8];
-            Uw[0] = Jh.C.xz;  Uw[1] = Jh.C.yz;  Uw[2] = Jh.C.zz;
-            const D Om = Jh.C.zz;
-            if (!dpositive(Om)) bad = 1;
-            invOm = drecip(Om);
-            {
-                const D vals[6] = {Uv[0], Uv[1], Uv[2], Uw[0], Uw[1], Uw[2]};
-#pragma unroll
-                for (int k = 0; k < 6; ++k) aba_zput(wsz, B, b, i, k, vals[k]);
-                aba_zput(wsz, B, b, i, 7, invOm);
-            }
-            if (i == 0) *jbad = bad;
-            __threadfence_block();
-            *progress = i;
-        }
-        return 0;
-    }
 
     // ---- warp Z. Sweep 1: bias motion (qdd = 0) and bias wrenches, base to tip
     Motion<TB> x;
@@ -185,14 +213,7 @@ __device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
         if constexpr (kExt) tau_hat = dcvt<D>(DF(__ldg(taur + i)) - F.n.z);
         else tau_hat = dsub_exact<D>(__ldg(taur + i), F.n.z);
         // U_i and 1 / Omega_i from warp J
-        for (int it = 0; !timeout && *progress > i; ++it) {
-            if (it >= kAbaPairSpinLimit) {
-                timeout = 1;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence_block();
+        aba_wait2(pu, pv, i, timeout);
 #pragma unroll
         for (int k = 0; k < 6; ++k) Up[k] = ldz(i, k);
         const D invOm = ldz(i, 7);
@@ -213,7 +234,9 @@ __device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
     }
 
     // Sweep 3: lambda and qdd, base to tip
-    int bad = *jbad;
+    const int jb = *jbu | *jbv;
+    int bad = jb & 1;
+    timeout |= (jb >> 1) & 1;
     V3<D> lv = mk3(D(0), D(0), D(0)), lw = mk3(D(0), D(0), D(0));
 #pragma unroll 1
     for (int i = 0; i < n; ++i) {
@@ -236,6 +259,31 @@ __device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
         qddr[i] = dcvt<T>(qdd_i);
     }
     return (bad ? RD_WARN_SINGULAR : 0) | (timeout ? RD_WARN_TIMEOUT : 0);
+}
+
+// One instance's share of the work for one of the two warps (role 0: J, role
+// 1: Z). The caller sets *progress to n or more (nothing published) and *jbad
+// to 0, and makes both visible to the pair, before either role starts. qr, qdr,
+// taur, qddr: the instance's rows; ws / wsz with (B, b): its workspace slots.
+// Role Z returns the status word, role J 0. The body synchronises with nothing
+// but its partner lane's progress counter: callers may run it on any subset of
+// a warp's lanes (fleets mix request kinds within a warp).
+template <typename T, typename D, typename TB, int TRIG>
+__device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
+                                             const D *__restrict__ sd,
+                                             const DF *__restrict__ sdf, int n,
+                                             const T *__restrict__ qr, const T *__restrict__ qdr,
+                                             const T *__restrict__ taur, T *__restrict__ qddr,
+                                             T *__restrict__ ws, D *__restrict__ wsz, int B,
+                                             int b, const BaseParams<T> &base,
+                                             volatile int *progress, int *jbad)
+{
+    if (role == 0) {
+        aba_pair_j<T, D, TB, TRIG>(sc, sd, sdf, n, qr, wsz, B, b, progress, jbad);
+        return 0;
+    }
+    return aba_pair_z<T, D, TB, TRIG>(sc, sd, sdf, n, qr, qdr, taur, qddr, ws, wsz, B, b, base,
+                                      progress, progress, jbad, jbad);
 }
 
 template <typename T, typename D, typename TB, int TRIG>

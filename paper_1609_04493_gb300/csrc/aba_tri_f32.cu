@@ -1,0 +1,25 @@
+// aba_tri_f32.cu -- instantiations of the three-warp forward-dynamics kernel
+// (aba_tri.cuh).
+#include "aba_pair_launch.cuh"
+
+int rd_aba_tri_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                   void *qdd, int *status, void *ws, const double *base18, bool fp64_update,
+                   bool extended_bias, cudaStream_t s)
+{
+    using rdyn::DF;
+    using rdyn::launch_aba_multi;
+    if (extended_bias)
+        return fp64_update
+                   ? launch_aba_multi<float, double, DF, 3>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+                   : launch_aba_multi<float, DF, DF, 3>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+    return fp64_update
+               ? launch_aba_multi<float, double, float, 3>(m, B, q, qd, tau, qdd, status, ws, base18, s)
+               : launch_aba_multi<float, DF, float, 3>(m, B, q, qd, tau, qdd, status, ws, base18, s);
+}
+
+int rd_aba_tri_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                   void *qdd, int *status, void *ws, const double *base18, cudaStream_t s)
+{
+    return rdyn::launch_aba_multi<double, double, double, 3>(m, B, q, qd, tau, qdd, status, ws,
+                                                             base18, s);
+}

@@ -107,6 +107,13 @@ int rd_aba_pair_f32(const rd_model *m, int B, const void *q, const void *qd, con
                     bool extended_bias, cudaStream_t s);
 int rd_aba_pair_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                     void *qdd, int *status, void *ws, const double *base18, cudaStream_t s);
+// the same with the articulated-inertia recursion split over two warps
+// (three warps per 32 instances, aba_tri.cuh)
+int rd_aba_tri_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                   void *qdd, int *status, void *ws, const double *base18, bool fp64_update,
+                   bool extended_bias, cudaStream_t s);
+int rd_aba_tri_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
+                   void *qdd, int *status, void *ws, const double *base18, cudaStream_t s);
 size_t rd_aba_ws_bytes_f32(int n, int B, int flags);
 size_t rd_aba_ws_bytes_f64(int n, int B, int flags);
 int rd_build_chain(int n, const double *M, const double *S, const double *inertia,
