@@ -105,11 +105,18 @@ enum rd_status {
  * block, exchanging their shift terms per link), three warps per 32 instances.
  * Same results to rounding; same exclusions. */
 #define RD_ABA_THREE_WARPS 0x100
+/* aba_batch test hook, only with RD_ABA_TWO_WARPS: the articulated-inertia warp
+ * withholds its per-link announcements, so every wait of the other warp runs
+ * out (one bounded wait per instance, a quarter of a second or more) and every
+ * status word carries RD_WARN_TIMEOUT. qdd is then undefined. It exists to
+ * test that path: no wait in the library is unbounded. */
+#define RD_ABA_TEST_WITHHOLD 0x40000000
 
 /* Per-instance status word of aba_batch (0 = fine); bits. */
 #define RD_WARN_SINGULAR 1 /* an Omega_i <= 0 or a non-finite qdd appeared */
-#define RD_WARN_TIMEOUT 2  /* two-warp mapping: a bounded wait for the other warp gave up
-                              (about a second); that instance's qdd is invalid */
+#define RD_WARN_TIMEOUT 2  /* two- or three-warp mapping (also fleets' warp pairs): a
+                              bounded wait for another warp gave up (a quarter of a
+                              second or more); that instance's qdd is invalid */
 
 /* Kernel variant for rnea_batch. */
 enum rd_variant {

@@ -417,6 +417,7 @@ RD_ABA_WARP_PER_INSTANCE = 0x20
 RD_ABA_THREAD_PER_INSTANCE = 0x40
 RD_ABA_TWO_WARPS = 0x80
 RD_ABA_THREE_WARPS = 0x100
+RD_ABA_TEST_WITHHOLD = 0x40000000
 RD_WARN_SINGULAR = 1
 RD_WARN_TIMEOUT = 2
 

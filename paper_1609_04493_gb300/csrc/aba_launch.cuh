@@ -256,6 +256,9 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
                                        "one another, and the first three RD_ABA_JOINT_FRAMES and "
                                        "RD_ABA_SCANS_IN_DTYPE");
     }
+    const bool withhold = (flags & RD_ABA_TEST_WITHHOLD) != 0;
+    if (withhold && !(flags & RD_ABA_TWO_WARPS))
+        return rd_fail(RD_ERR_ARG, "aba_batch: RD_ABA_TEST_WITHHOLD needs RD_ABA_TWO_WARPS");
     if (aba_use_tri<T>(m->n, B, flags, ext)) {
         if constexpr (sizeof(T) == 4)
             return rd_aba_tri_f32(m, B, q, qd, tau, qdd, status, ws, base18,
@@ -266,9 +269,9 @@ int aba_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
     if (aba_use_pair<T>(m->n, B, flags)) {
         if constexpr (sizeof(T) == 4)
             return rd_aba_pair_f32(m, B, q, qd, tau, qdd, status, ws, base18,
-                                   (flags & RD_ABA_FP64_UPDATE) != 0, ext, s);
+                                   (flags & RD_ABA_FP64_UPDATE) != 0, ext, withhold, s);
         else
-            return rd_aba_pair_f64(m, B, q, qd, tau, qdd, status, ws, base18, s);
+            return rd_aba_pair_f64(m, B, q, qd, tau, qdd, status, ws, base18, withhold, s);
     }
     if (aba_use_warp<T>(m->n, B, flags)) {
         if constexpr (sizeof(T) == 4)

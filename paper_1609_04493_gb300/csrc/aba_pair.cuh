@@ -286,14 +286,18 @@ __device__ __forceinline__ int aba_pair_role(int role, const T *__restrict__ sc,
                                       progress, progress, jbad, jbad);
 }
 
+// withhold (a test hook, RD_ABA_TEST_WITHHOLD): warp J publishes into a counter
+// that warp Z does not read, so every wait of warp Z runs out and reports
+// RD_WARN_TIMEOUT.
 template <typename T, typename D, typename TB, int TRIG>
 __global__ void __launch_bounds__(64)
 aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__restrict__ sdf,
                 int n, int B, const T *__restrict__ q, const T *__restrict__ qd,
                 const T *__restrict__ tau, T *__restrict__ qdd_out, int *__restrict__ status,
-                T *__restrict__ ws, D *__restrict__ wsz, BaseParams<T> base)
+                T *__restrict__ ws, D *__restrict__ wsz, BaseParams<T> base, int withhold)
 {
     __shared__ volatile int progress[32];
+    __shared__ volatile int withheld[32];
     __shared__ int jbad[32];
     const int role = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -307,7 +311,9 @@ aba_pair_kernel(const T *__restrict__ sc, const D *__restrict__ sd, const DF *__
     const size_t row = (size_t)b * (size_t)n;
     const int st = aba_pair_role<T, D, TB, TRIG>(role, sc, sd, sdf, n, q + row, qd + row, tau + row,
                                                  qdd_out + row, ws, wsz, B, b, base,
-                                                 &progress[lane], &jbad[lane]);
+                                                 (role == 0 && withhold) ? &withheld[lane]
+                                                                         : &progress[lane],
+                                                 &jbad[lane]);
     if (role == 1 && status) status[b] = st;
 }
 

@@ -12,9 +12,11 @@ namespace rdyn {
 
 // One block per 32 instances, WARPS warps per block. Workspace: the sweep-1
 // state in the bias precision TB, then (256-byte aligned) the solve state in D.
+// withhold: the two-warp kernel's test hook (aba_pair_kernel).
 template <typename T, typename D, typename TB, int WARPS>
 int launch_aba_multi(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
-                     void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream)
+                     void *qdd, int *status, void *ws, const double *base18, cudaStream_t stream,
+                     bool withhold = false)
 {
     static_assert(WARPS == 2 || WARPS == 3, "two or three warps per 32 instances");
     const int n = m->n;
@@ -40,7 +42,7 @@ int launch_aba_multi(const rd_model *m, int B, const void *q, const void *qd, co
         aba_pair_kernel<T, D, TB, kTrigPoly><<<grid, 64, 0, stream>>>(
             sc, sd, sdf, n, B, static_cast<const T *>(q), static_cast<const T *>(qd),
             static_cast<const T *>(tau), static_cast<T *>(qdd), status, static_cast<T *>(ws), wsz,
-            bp);
+            bp, withhold ? 1 : 0);
     else
         aba_tri_kernel<T, D, TB, kTrigPoly><<<grid, 96, 0, stream>>>(
             sc, sd, sdf, n, B, static_cast<const T *>(q), static_cast<const T *>(qd),

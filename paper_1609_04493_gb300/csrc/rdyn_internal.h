@@ -101,12 +101,14 @@ int rd_aba_warp_f32(const rd_model *m, int B, const void *q, const void *qd, con
                     bool extended_bias, cudaStream_t s);
 int rd_aba_warp_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                     void *qdd, int *status, const double *base18, cudaStream_t s);
-// forward dynamics with two warps per 32 instances (aba_pair.cuh)
+// forward dynamics with two warps per 32 instances (aba_pair.cuh); withhold:
+// the RD_ABA_TEST_WITHHOLD hook
 int rd_aba_pair_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
                     void *qdd, int *status, void *ws, const double *base18, bool fp64_update,
-                    bool extended_bias, cudaStream_t s);
+                    bool extended_bias, bool withhold, cudaStream_t s);
 int rd_aba_pair_f64(const rd_model *m, int B, const void *q, const void *qd, const void *tau,
-                    void *qdd, int *status, void *ws, const double *base18, cudaStream_t s);
+                    void *qdd, int *status, void *ws, const double *base18, bool withhold,
+                    cudaStream_t s);
 // the same with the articulated-inertia recursion split over two warps
 // (three warps per 32 instances, aba_tri.cuh)
 int rd_aba_tri_f32(const rd_model *m, int B, const void *q, const void *qd, const void *tau,

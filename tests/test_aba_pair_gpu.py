@@ -164,3 +164,37 @@ def test_auto_picks_the_measured_mapping(cuda_lib, n, B, prec, expect):
     flag = {"two": cuda_lib.RD_ABA_TWO_WARPS, "three": cuda_lib.RD_ABA_THREE_WARPS}[expect]
     pick = cuda_lib.aba(model, *x, flags=prec | flag)
     assert torch.equal(auto, pick)
+
+
+def test_bounded_wait_runs_out_and_reports(cuda_lib):
+    """RD_ABA_TEST_WITHHOLD: warp J announces nothing, so warp Z's bounded wait
+    runs out once per instance; the call returns, every status word carries
+    RD_WARN_TIMEOUT, and the context stays usable (the next call matches the
+    oracle). No wait in the library is unbounded."""
+    import torch
+
+    ch = chaingen.make_chain(8, seed=3)
+    model = cuda_lib.Model(ch)
+    st = chaingen.make_states(40, 8, seed=2, kinds=("q", "qd", "tau"))
+    x = [torch.from_numpy(st[k].astype(np.float32)).cuda() for k in ("q", "qd", "tau")]
+    status = torch.full((40,), -7, dtype=torch.int32, device="cuda")
+    cuda_lib.aba(model, *x, status=status,
+                 flags=cuda_lib.RD_ABA_TWO_WARPS | cuda_lib.RD_ABA_TEST_WITHHOLD)
+    torch.cuda.synchronize()
+    assert torch.all((status & cuda_lib.RD_WARN_TIMEOUT) != 0)
+    ok = torch.full((40,), -7, dtype=torch.int32, device="cuda")
+    qdd = cuda_lib.aba(model, *x, status=ok, flags=cuda_lib.RD_ABA_TWO_WARPS).cpu().double().numpy()
+    assert torch.all(ok == 0)
+    h = {k: st[k].astype(np.float32).astype(np.float64) for k in ("q", "qd", "tau")}
+    ref = oracle.fd_aba(ch, h["q"], h["qd"], h["tau"])
+    assert oracle.rel_err(qdd, ref) <= TOL["float32"]
+
+
+def test_withhold_hook_needs_two_warps(cuda_lib):
+    import torch
+
+    model = cuda_lib.Model(chaingen.make_chain(6))
+    x = torch.zeros((4, 6), device="cuda")
+    for other in (0, cuda_lib.RD_ABA_THREE_WARPS, cuda_lib.RD_ABA_THREAD_PER_INSTANCE):
+        with pytest.raises(cuda_lib.RdError):
+            cuda_lib.aba(model, x, x, x, flags=cuda_lib.RD_ABA_TEST_WITHHOLD | other)
