@@ -423,6 +423,10 @@ enum rd_schedule {
  * recursion and one on the rest (as RD_ABA_TWO_WARPS); threads per block must
  * then be a multiple of 64 up to 448. */
 #define RD_FLEET_TWO_WARPS(min_links) ((min_links) << 16)
+/* As RD_FLEET_TWO_WARPS with three warps per 32 requests (as RD_ABA_THREE_WARPS);
+ * the tune word's 2^t threads per block then name 2^t / 64 triples (t = 6 or 7:
+ * 96 or 192 threads). */
+#define RD_FLEET_THREE_WARPS(min_links) (((min_links) << 16) | (1 << 24))
 
 /*
  * rd_fleet_create -- upload nrobots chains (Sec. II-A model per robot).

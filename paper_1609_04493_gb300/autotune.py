@@ -124,8 +124,8 @@ def tune_rnea(model, q, qd, qdd, out=None, reps=5, use_cache=True):
 def fleet_candidates():
     """(schedule, tune) pairs: one launch per group; the persistent kernel at
     several block shapes with one thread per request; and the persistent kernel
-    with two warps per 32 forward-dynamics requests for the groups whose chains
-    reach a threshold (the warps per request of each n-range)."""
+    with two or three warps per 32 forward-dynamics requests for the groups whose
+    chains reach a threshold (the warps per request of each n-range)."""
     c = [(b.RD_SCHED_PER_GROUP, 0)]
     for lt in (5, 6, 7, 8):
         for per_sm in (1, 2, 4, 8):
@@ -137,6 +137,11 @@ def fleet_candidates():
                 if (1 << lt) * per_sm <= 1024:
                     c.append((b.RD_SCHED_PERSISTENT,
                               b.RD_FLEET_TUNE(lt, per_sm) | b.RD_FLEET_TWO_WARPS(min_links)))
+    for min_links in (33, 65):
+        for lt in (6, 7):
+            for per_sm in (1, 2, 4):
+                c.append((b.RD_SCHED_PERSISTENT,
+                          b.RD_FLEET_TUNE(lt, per_sm) | b.RD_FLEET_THREE_WARPS(min_links)))
     return c
 
 

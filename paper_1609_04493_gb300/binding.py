@@ -476,6 +476,10 @@ def RD_FLEET_TWO_WARPS(min_links):
     return int(min_links) << 16
 
 
+def RD_FLEET_THREE_WARPS(min_links):
+    return (int(min_links) << 16) | (1 << 24)
+
+
 def _iptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
 

@@ -27,6 +27,7 @@
 
 #include "aba_dh.cuh"
 #include "aba_pair.cuh"
+#include "aba_tri.cuh"
 #include "rnea_dhp.cuh"
 
 namespace rdyn {
@@ -54,8 +55,9 @@ struct FleetArgs {
     // double-float (FP32 data, chains beyond RD_ABA_EXTENDED_BIAS_LINKS)
     const DF *records_df;
     int ext_groups;
-    // two-warp forward dynamics (fleet_pair_kernel): the first pair_groups
-    // groups of 32 sorted requests, taken through pair_counter
+    // two- or three-warp forward dynamics (fleet_pair_kernel,
+    // fleet_tri_kernel): the first pair_groups groups of 32 sorted requests,
+    // taken through pair_counter
     int pair_groups;
     int *pair_counter;
     int R;
@@ -223,6 +225,99 @@ __device__ __forceinline__ void fleet_request_pair(const FleetArgs<T, D> &a, int
 __device__ __forceinline__ void pair_barrier(int id)
 {
     asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+__device__ __forceinline__ void triple_barrier(int id)
+{
+    asm volatile("bar.sync %0, 96;" ::"r"(id) : "memory");
+}
+
+// The request at sorted position k for one warp of a triple (role 0: JA, 1: JB,
+// 2: Z; aba_tri.cuh). An inverse-dynamics request runs on role 0 alone.
+template <typename T, typename D>
+__device__ __forceinline__ void fleet_request_tri(const FleetArgs<T, D> &a, int k, int role,
+                                                  AbaTriShared<D> &sh, int lane)
+{
+    const int r = a.order[k];
+    const int robot = a.req_robot[r];
+    const int n = a.robot_n[robot];
+    const long long lo = a.robot_link[robot];
+    const long long off = a.req_off[r];
+    if (a.req_kind[r] == 0) {
+        if (role == 0) fleet_request(a, k);
+        return;
+    }
+    const T *sc = a.consts + lo * kDhConsts;
+    const D *sd = a.records + lo * kAbaDh64;
+    const DF *sdf = a.records_df ? a.records_df + lo * kAbaDh64 : nullptr;
+    const int g = k >> 5;
+    T *wt = reinterpret_cast<T *>(a.ws + a.group_ws[g]);
+    D *wz = reinterpret_cast<D *>(a.ws + a.group_wz[g]);
+    const int b = k & 31;
+    auto body = [&](auto tb_tag) {
+        using TB = decltype(tb_tag);
+        if (role == 0) {
+            aba_tri_ja<T, D, TB, kTrigPoly>(sc, sd, sdf, n, a.q + off, wz, 32, b, sh, lane);
+        } else if (role == 1) {
+            aba_tri_jb<T, D, TB, kTrigPoly>(sc, sd, sdf, n, a.q + off, wz, 32, b, sh, lane);
+        } else {
+            BaseParams<T> bp;
+            fleet_base(a, robot, bp);
+            const volatile int *cnt = &sh.cnt[0][0];
+            const int st = aba_pair_z<T, D, TB, kTrigPoly>(
+                sc, sd, sdf, n, a.q + off, a.qd + off, a.in2 + off, a.out + off, wt, wz, 32, b, bp,
+                cnt + kTriUA * 32 + lane, cnt + kTriUB * 32 + lane, &sh.flags[0][lane],
+                &sh.flags[1][lane]);
+            if (a.status) a.status[r] = st ? 1 : 0;
+        }
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (g < a.ext_groups) {
+            body(DF{});
+            return;
+        }
+    }
+    body(T{});
+}
+
+// Persistent with three-warp forward dynamics: as fleet_pair_kernel with warp
+// triples (JA, JB, Z) per group of 32 sorted requests, at most two triples per
+// block (96 or 192 threads; named barriers 1..4; 13 KB of exchange state per
+// triple), then every warp on the remaining requests.
+template <typename T, typename D>
+__global__ void fleet_tri_kernel(FleetArgs<T, D> a)
+{
+    __shared__ AbaTriShared<D> sh[2];
+    __shared__ volatile int grp[2];
+    const int tri = threadIdx.x / 96;
+    const int role = (threadIdx.x >> 5) % 3;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (role == 0) {
+            if (lane == 0) grp[tri] = atomicAdd(a.pair_counter, 1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[tri].cnt[c][lane] = INT_MAX;
+            sh[tri].flags[0][lane] = 0;
+            sh[tri].flags[1][lane] = 0;
+        }
+        __syncwarp();
+        triple_barrier(1 + 2 * tri);
+        const int g = grp[tri];
+        if (g >= a.pair_groups) break;
+        const int k = 32 * g + lane;
+        if (k < a.R) fleet_request_tri(a, k, role, sh[tri], lane);
+        __syncwarp();
+        triple_barrier(2 + 2 * tri);
+    }
+    const int base = 32 * a.pair_groups;
+    for (;;) {
+        int start = 0;
+        if (lane == 0) start = base + atomicAdd(a.counter, 32);
+        start = __shfl_sync(0xffffffffu, start, 0);
+        if (start >= a.R) break;
+        const int k = start + lane;
+        if (k < a.R) fleet_request(a, k);
+    }
 }
 
 // Persistent with two-warp forward dynamics. Warps 2p and 2p + 1 of a block form

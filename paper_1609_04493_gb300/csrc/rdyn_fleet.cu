@@ -275,10 +275,12 @@ extern "C" int rd_plan_groups(const rd_plan *p) { return p ? (int)p->groups.size
 namespace {
 
 // pair_n > 0: forward-dynamics groups whose first chain has at least pair_n
-// links run two warps per 32 requests (fleet_pair_kernel)
+// links run two warps per 32 requests (fleet_pair_kernel), or three with
+// three_warps (fleet_tri_kernel)
 template <typename T, typename D>
 int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, void *out,
-              const double *b18, int *status, int schedule, int tune, int pair_n, cudaStream_t s)
+              const double *b18, int *status, int schedule, int tune, int pair_n,
+              bool three_warps, cudaStream_t s)
 {
     const rd_fleet *f = p->fleet;
     rdyn::FleetArgs<T, D> a;
@@ -327,12 +329,23 @@ int run_fleet(const rd_plan *p, const void *q, const void *qd, const void *in2, 
         a.pair_groups = pg;
         int threads = (tune >> 8) & 0xff ? 1 << ((tune >> 8) & 0xff) : 128;
         int per_sm = tune & 0xff ? tune & 0xff : 4;
-        if (threads < 64 || threads > 448 || threads % 64)
+        if (three_warps) {
+            // 2^t threads name 2^t / 64 groups per block, as for pairs: 1 or 2
+            if (threads != 64 && threads != 128)
+                return rd_fail(RD_ERR_ARG, "fleet_batch: the three-warp schedule takes one or two "
+                                           "triples per block (tune threads 64 or 128, got %d)",
+                               threads);
+            threads = 96 * (threads / 64);
+        } else if (threads < 64 || threads > 448 || threads % 64) {
             return rd_fail(RD_ERR_ARG, "fleet_batch: the two-warp schedule takes 64..448 threads "
                                        "per block in multiples of 64 (%d)", threads);
+        }
         e = cudaMemsetAsync(p->counter, 0, 2 * sizeof(int), s);
         if (e != cudaSuccess) return rd_cuda_fail(e, "fleet_batch: counter reset");
-        rdyn::fleet_pair_kernel<T, D><<<p->sms * per_sm, threads, 0, s>>>(a);
+        if (three_warps)
+            rdyn::fleet_tri_kernel<T, D><<<p->sms * per_sm, threads, 0, s>>>(a);
+        else
+            rdyn::fleet_pair_kernel<T, D><<<p->sms * per_sm, threads, 0, s>>>(a);
     } else if (schedule == RD_SCHED_PERSISTENT) {
         int threads = (tune >> 8) & 0xff ? 1 << ((tune >> 8) & 0xff) : 128;
         int per_sm = tune & 0xff ? tune & 0xff : 4;
@@ -384,13 +397,19 @@ extern "C" int fleet_batch(const rd_plan *p, const void *q, const void *qd, cons
     const bool fp64_update = (schedule & RD_FLEET_FP64_UPDATE) != 0;
     schedule &= ~RD_FLEET_FP64_UPDATE;
     const int pair_n = (tune >> 16) & 0xff;
-    if (pair_n && schedule != RD_SCHED_PERSISTENT)
-        return rd_fail(RD_ERR_ARG, "fleet_batch: two-warp forward dynamics needs the persistent "
-                                   "schedule");
+    const bool three = ((tune >> 24) & 1) != 0;
+    if ((pair_n || three) && schedule != RD_SCHED_PERSISTENT)
+        return rd_fail(RD_ERR_ARG, "fleet_batch: two- or three-warp forward dynamics needs the "
+                                   "persistent schedule");
+    if (three && !pair_n)
+        return rd_fail(RD_ERR_ARG, "fleet_batch: RD_FLEET_THREE_WARPS needs a chain length");
     if (p->dtype == RD_F32) {
         if (fp64_update)
-            return run_fleet<float, double>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n, s);
-        return run_fleet<float, rdyn::DF>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n, s);
+            return run_fleet<float, double>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n,
+                                            three, s);
+        return run_fleet<float, rdyn::DF>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n,
+                                          three, s);
     }
-    return run_fleet<double, double>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n, s);
+    return run_fleet<double, double>(p, q, qd, in2, out, b18, status, schedule, tune, pair_n,
+                                     three, s);
 }

@@ -20,18 +20,25 @@ def test_rnea_candidates_respect_lane_capacity():
 def test_fleet_candidates_fit_a_cta():
     """Bits 0..7 of the tune word: blocks per SM; 8..15: log2 threads per block;
     16..23: the chain length from which forward-dynamics groups take two warps
-    (such blocks hold whole warp pairs, at most 7 of them)."""
-    pairs = 0
+    (such blocks hold whole warp pairs, at most 7 of them); bit 24: three warps
+    instead (2^t / 64 triples per block, one or two)."""
+    pairs = triples = 0
     for sched, tune in autotune.fleet_candidates():
         if sched == b.RD_SCHED_PERSISTENT:
             threads = 1 << ((tune >> 8) & 0xff)
             assert threads * (tune & 0xff) <= 1024
-            if tune >> 16:
+            length = (tune >> 16) & 0xff
+            if tune >> 24:
+                triples += 1
+                assert threads in (64, 128) and length > 0
+                assert tune == b.RD_FLEET_TUNE((tune >> 8) & 0xff, tune & 0xff) | \
+                    b.RD_FLEET_THREE_WARPS(length)
+            elif length:
                 pairs += 1
                 assert threads % 64 == 0 and threads <= 448
                 assert tune == b.RD_FLEET_TUNE((tune >> 8) & 0xff, tune & 0xff) | \
-                    b.RD_FLEET_TWO_WARPS(tune >> 16)
-    assert pairs
+                    b.RD_FLEET_TWO_WARPS(length)
+    assert pairs and triples
 
 
 def test_rnea_candidates_hybrid_store_fewer_links_than_the_chain():

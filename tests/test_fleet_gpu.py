@@ -182,8 +182,9 @@ def test_fleet_uneven_workload_at_full_size(cuda_lib):
         refs[r] = fn(reqs[r]["chain"], h64[0][sl][None], h64[1][sl][None], h64[2][sl][None])
     f64 = rd.RD_FLEET_FP64_UPDATE
     pair = rd.RD_FLEET_TUNE(7, 2) | rd.RD_FLEET_TWO_WARPS(33)
+    tri = rd.RD_FLEET_TUNE(7, 2) | rd.RD_FLEET_THREE_WARPS(65)
     for schedule, tune in ((0 | f64, 0), (rd.RD_SCHED_PER_GROUP | f64, 0), (0, 0), (0 | f64, pair),
-                           (0, pair)):
+                           (0, pair), (0 | f64, tri)):
         out = rd.fleet_batch(plan, *x, schedule=schedule, tune=tune).cpu().numpy().astype(np.float64)
         worst = {0: 0.0, 1: 0.0}
         for r in sample:
@@ -194,15 +195,18 @@ def test_fleet_uneven_workload_at_full_size(cuda_lib):
         assert worst[1] <= TOL_FD["float32"], (schedule, tune, worst)
 
 
+@pytest.mark.parametrize("warps", [2, 3])
 @pytest.mark.parametrize("dtype", ["float32", "float64"])
 @pytest.mark.parametrize("min_links", [1, 33, 65])
-def test_fleet_two_warp_forward_dynamics(cuda_lib, dtype, min_links):
-    """RD_FLEET_TWO_WARPS: forward-dynamics groups from a length on run two warps
-    per 32 requests; every request against the oracle, and against the
-    one-thread-per-request schedule (FP64 to rounding, FP32 to a few ulps)."""
+def test_fleet_two_warp_forward_dynamics(cuda_lib, dtype, min_links, warps):
+    """RD_FLEET_TWO_WARPS / RD_FLEET_THREE_WARPS: forward-dynamics groups from a
+    length on run two or three warps per 32 requests; every request against the
+    oracle, and against the one-thread-per-request schedule (FP64 to rounding,
+    FP32 to a few ulps)."""
     reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 700, 2, 100, dtype, seed=31,
                                                 fd_fraction=0.4)
-    tune = cuda_lib.RD_FLEET_TUNE(7, 2) | cuda_lib.RD_FLEET_TWO_WARPS(min_links)
+    split = cuda_lib.RD_FLEET_TWO_WARPS if warps == 2 else cuda_lib.RD_FLEET_THREE_WARPS
+    tune = cuda_lib.RD_FLEET_TUNE(7, 2) | split(min_links)
     out = cuda_lib.fleet_batch(plan, *dev, tune=tune).cpu().numpy().astype(np.float64)
     check(reqs, plan, kinds, host, out, dtype)
     ref = cuda_lib.fleet_batch(plan, *dev).cpu().numpy().astype(np.float64)
@@ -210,13 +214,15 @@ def test_fleet_two_warp_forward_dynamics(cuda_lib, dtype, min_links):
     assert np.max(np.abs(out - ref)) <= (1e-10 if dtype == "float64" else 1e-5) * scale
 
 
-def test_fleet_two_warps_fp64_update_and_status(cuda_lib):
+@pytest.mark.parametrize("warps", [2, 3])
+def test_fleet_two_warps_fp64_update_and_status(cuda_lib, warps):
     import torch
 
     reqs, fleet, plan, kinds, host, dev = build(cuda_lib, 300, 40, 100, "float32", seed=33,
                                                 fd_fraction=0.5)
     status = torch.full((300,), -1, dtype=torch.int32, device="cuda")
-    tune = cuda_lib.RD_FLEET_TUNE(6, 4) | cuda_lib.RD_FLEET_TWO_WARPS(6)
+    split = cuda_lib.RD_FLEET_TWO_WARPS if warps == 2 else cuda_lib.RD_FLEET_THREE_WARPS
+    tune = cuda_lib.RD_FLEET_TUNE(6, 4) | split(6)
     out = cuda_lib.fleet_batch(plan, *dev, status=status, tune=tune,
                                schedule=cuda_lib.RD_FLEET_FP64_UPDATE)
     check(reqs, plan, kinds, host, out.cpu().numpy().astype(np.float64), "float32")
@@ -233,3 +239,13 @@ def test_fleet_two_warps_rejects_bad_shapes(cuda_lib):
     with pytest.raises(cuda_lib.RdError):
         cuda_lib.fleet_batch(plan, *dev, schedule=cuda_lib.RD_SCHED_PER_GROUP,
                              tune=cuda_lib.RD_FLEET_TWO_WARPS(6))
+    # three warps: one or two triples per block (tune threads 64 or 128), a
+    # chain length, the persistent schedule
+    for tune in (cuda_lib.RD_FLEET_TUNE(8, 1) | cuda_lib.RD_FLEET_THREE_WARPS(6),
+                 cuda_lib.RD_FLEET_TUNE(5, 1) | cuda_lib.RD_FLEET_THREE_WARPS(6),
+                 cuda_lib.RD_FLEET_TUNE(7, 1) | (1 << 24)):
+        with pytest.raises(cuda_lib.RdError):
+            cuda_lib.fleet_batch(plan, *dev, tune=tune)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.fleet_batch(plan, *dev, schedule=cuda_lib.RD_SCHED_PER_GROUP,
+                             tune=cuda_lib.RD_FLEET_THREE_WARPS(6))
