@@ -149,7 +149,7 @@ def parse_args():
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
     p.add_argument("--kernel-only",
                    choices=["f32", "f64", "f64df", "host", "vjp", "vjplane", "aba", "aba64",
-                            "abawarp", "abapair", "abatri", "fleet"],
+                            "abawarp", "abapair", "abatri", "fleet", "fleetpair", "fleettri64"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
@@ -158,7 +158,9 @@ def parse_args():
                         "per instance; aba: forward dynamics n=64 B=16384 (double-float updates; "
                         "aba64: FP64 updates); abawarp: forward dynamics n=64 B=1024, one warp per "
                         "instance; abapair / abatri: forward dynamics n=64 B=16384, two / three "
-                        "warps per 32 instances; fleet: 20000 mixed requests)")
+                        "warps per 32 instances; fleet: 20000 mixed requests; fleetpair: the same "
+                        "with warp pairs for forward-dynamics chains from 65 links; fleettri64: "
+                        "warp triples from 65 links, FP64 updates)")
     return p.parse_args()
 
 
@@ -873,8 +875,13 @@ def run_kernel_only(args):
         J = plan.total_joints
         x = [torch.from_numpy(a.astype(np.float32)).to(dev)
              for a in (rng.uniform(-np.pi, np.pi, J), rng.normal(0, 1, J), rng.normal(0, 5, J))]
+        sched, tune = {"fleet": (0, rd.RD_FLEET_TUNE(7, 1)),
+                       "fleetpair": (0, rd.RD_FLEET_TUNE(7, 2) | rd.RD_FLEET_TWO_WARPS(65)),
+                       "fleettri64": (rd.RD_FLEET_FP64_UPDATE,
+                                      rd.RD_FLEET_TUNE(7, 2) | rd.RD_FLEET_THREE_WARPS(65)),
+                       }[args.kernel_only]
         for _ in range(calls):
-            res = rd.fleet_batch(plan, *x, tune=rd.RD_FLEET_TUNE(7, 1))
+            res = rd.fleet_batch(plan, *x, schedule=sched, tune=tune)
     torch.cuda.synchronize()
     print(f"kernel-only {args.kernel_only}: {calls} launches, max|out| = "
           f"{float(res.abs().max()):.4g}")

@@ -198,3 +198,17 @@ def test_withhold_hook_needs_two_warps(cuda_lib):
     for other in (0, cuda_lib.RD_ABA_THREE_WARPS, cuda_lib.RD_ABA_THREAD_PER_INSTANCE):
         with pytest.raises(cuda_lib.RdError):
             cuda_lib.aba(model, x, x, x, flags=cuda_lib.RD_ABA_TEST_WITHHOLD | other)
+
+
+@pytest.mark.parametrize("prec", [0, 0x4])
+@pytest.mark.parametrize("n", [16, 64])
+def test_bench_fd_configuration_sampled(cuda_lib, n, prec):
+    """The bench's forward-dynamics lines as launched: FP32 data, B = 16384, no
+    mapping flag (the library picks two warps per 32 instances at this batch),
+    double-float or FP64 updates (RD_ABA_FP64_UPDATE); every 64th instance
+    against the oracle, the rest finite."""
+    qdd, ch, h, _ = run(cuda_lib, n, 16384, "float32", seed=6000, flags=prec, mapping=0)
+    assert np.all(np.isfinite(qdd))
+    idx = np.arange(0, 16384, 64)
+    ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
+    assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
