@@ -148,14 +148,16 @@ def parse_args():
     p.add_argument("--quick", action="store_true", help="skip auxiliary measurements")
     p.add_argument("--no-uneven", action="store_true", help="skip the 100000-request workload")
     p.add_argument("--kernel-only",
-                   choices=["f32", "f64", "f64df", "host", "vjp", "vjplane", "aba", "aba64",
+                   choices=["f32", "f64", "f64df", "host", "vjp", "vjplane", "vjppair", "vjpsmem",
+                            "aba", "aba64",
                             "abawarp", "abapair", "abatri", "fleet", "fleetpair", "fleettri64"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
                         "arithmetic; host: rnea_batch_host on pinned FP32 arrays, the same "
                         "size; vjp: adjoint n=32 B=8192; vjplane: adjoint n=32 B=4096, 8 lanes "
-                        "per instance; aba: forward dynamics n=64 B=16384 (double-float updates; "
+                        "per instance; vjppair / vjpsmem: adjoint n=32 B=8192, two warps per 32 "
+                        "instances / state in shared memory; aba: forward dynamics n=64 B=16384 (double-float updates; "
                         "aba64: FP64 updates); abawarp: forward dynamics n=64 B=1024, one warp per "
                         "instance; abapair / abatri: forward dynamics n=64 B=16384, two / three "
                         "warps per 32 instances; fleet: 20000 mixed requests; fleetpair: the same "
@@ -363,7 +365,8 @@ class Peaks:
 def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
     """Seconds per rnea_vjp call at n = 32 FP32: recompute (the library's
     mapping) at B = 4096, 8192 and 262144, store at 8192, and at 8192 each
-    mapping by flag: one thread, shared-memory state, 8 lanes, two warps."""
+    mapping by flag: one thread, shared-memory state, 8 lanes, two warps, two
+    warps with shared-memory state."""
     raw = {}
     R = rd.RD_VJP_RECOMPUTE
     for B, mode in ((4096, R), (8192, R), (262144, R), (8192, rd.RD_VJP_STORE)):
@@ -391,7 +394,8 @@ def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
                 nm: timed(R | fl) for nm, fl in (("one_us", rd.RD_VJP_FLAG_ONE_THREAD),
                                                  ("smem_us", rd.RD_VJP_FLAG_SHARED_STATE),
                                                  ("lanes_us", rd.RD_VJP_FLAG_LANES),
-                                                 ("pair_us", rd.RD_VJP_FLAG_TWO_WARPS))}
+                                                 ("pair_us", rd.RD_VJP_FLAG_TWO_WARPS),
+                                                 ("duo_us", rd.RD_VJP_FLAG_TWO_WARPS_SHARED))}
     return raw
 
 
@@ -842,10 +846,13 @@ def run_kernel_only(args):
         res = torch.empty_like(host[0]).pin_memory()
         for _ in range(calls):
             rd.rnea_host(model, *host, out=res)
-    elif args.kernel_only in ("vjp", "vjplane"):
+    elif args.kernel_only in ("vjp", "vjplane", "vjppair", "vjpsmem"):
         lanes = args.kernel_only == "vjplane"
         Bv = 4096 if lanes else 8192
-        mode = rd.RD_VJP_RECOMPUTE | (rd.RD_VJP_FLAG_LANES if lanes else rd.RD_VJP_FLAG_ONE_THREAD)
+        mode = rd.RD_VJP_RECOMPUTE | {"vjp": rd.RD_VJP_FLAG_ONE_THREAD,
+                                      "vjplane": rd.RD_VJP_FLAG_LANES,
+                                      "vjppair": rd.RD_VJP_FLAG_TWO_WARPS,
+                                      "vjpsmem": rd.RD_VJP_FLAG_SHARED_STATE}[args.kernel_only]
         model = rd.Model(chaingen.make_chain(N_LINKS, seed=chaingen.BASE_SEED))
         st = chaingen.make_states(Bv, N_LINKS, seed=5000, kinds=("q", "qd", "qdd", "w"))
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]

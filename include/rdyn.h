@@ -293,6 +293,13 @@ enum rd_vjp_mode {
  * in the block's shared memory instead of re-deriving them in the reverse
  * sweep (no workspace). Without it the library picks by the batch size. */
 #define RD_VJP_FLAG_SHARED_STATE 0x4000
+/* OR-able into the mode of rnea_vjp, FP32 in RD_VJP_RECOMPUTE (or AUTO), whole
+ * 16-byte chunks, n <= 64: two warps per 32 instances with the per-link state
+ * in shared memory. One warp carries the motion, the wrench F and dVbar, the
+ * other the adjoint weight Fb and Vbar (with its own copy of the dVbar carry);
+ * they exchange nothing inside a sweep and combine their gradient terms at the
+ * end. Excludes the other mapping flags. */
+#define RD_VJP_FLAG_TWO_WARPS_SHARED 0x8000
 
 /*
  * rnea_vjp -- vector-Jacobian product of inverse dynamics for B states:

@@ -36,6 +36,7 @@ RD_VJP_FLAG_ONE_THREAD = 0x400
 RD_VJP_FLAG_LANES = 0x100
 RD_VJP_FLAG_LANES4 = 0x200
 RD_VJP_FLAG_SHARED_STATE = 0x4000
+RD_VJP_FLAG_TWO_WARPS_SHARED = 0x8000
 
 
 def RD_VARIANT_SCAN(lanes):

@@ -9,6 +9,7 @@
 #include "rdyn_internal.h"
 #include "rnea_vjp.cuh"
 #include "rnea_vjp_dh.cuh"
+#include "rnea_vjp_duo.cuh"
 #include "rnea_vjp_pair.cuh"
 
 namespace rdyn {
@@ -141,6 +142,46 @@ int launch_vjp_pair_k(const rd_model *m, int B, const void *q, const void *qd, c
     return RD_OK;
 }
 
+// Two warps per 32 instances with the state in shared memory (rnea_vjp_duo.cuh).
+template <int NMAX, int TRIG>
+int launch_vjp_duo_k(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
+                     const void *w, void *gq, void *gqd, void *gqdd, const double *base18,
+                     cudaStream_t stream)
+{
+    double b[18];
+    rd_convert_base_dh(m, base18, b);
+    BaseParams<float> bp;
+    for (int k = 0; k < 6; ++k) {
+        bp.V0[k] = (float)b[k];
+        bp.dV0[k] = (float)b[6 + k];
+        bp.Fn[k] = (float)b[12 + k];
+    }
+    DhParamConsts<float, NMAX> pc;
+    for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (float)m->host_dh64[k];
+    for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = 0.0f;
+    const size_t smem = vjp_duo_smem(m->n);
+    if (smem > (size_t)vjp_max_smem(m->device))
+        return rd_fail(RD_ERR_ARG, "rnea_vjp: the two-warp shared-state kernel needs %zu bytes of "
+                                   "shared memory per block at n = %d", smem, m->n);
+    static std::atomic<uint64_t> configured{0};
+    const uint64_t bit = 1ull << (m->device & 63);
+    if (smem > 48 * 1024 && !(configured.load() & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(rnea_vjp_duo_kernel<NMAX, TRIG>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             vjp_max_smem(m->device));
+        if (e != cudaSuccess) return rd_cuda_fail(e, "cudaFuncSetAttribute");
+        configured.fetch_or(bit);
+    }
+    const unsigned grid = (unsigned)((B + 31) / 32);
+    rnea_vjp_duo_kernel<NMAX, TRIG><<<grid, 64, smem, stream>>>(
+        pc, m->n, B, static_cast<const float *>(q), static_cast<const float *>(qd),
+        static_cast<const float *>(qdd), static_cast<const float *>(w), static_cast<float *>(gq),
+        static_cast<float *>(gqd), static_cast<float *>(gqdd), bp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return rd_cuda_fail(e, "rnea_vjp two-warp shared-state kernel launch");
+    return RD_OK;
+}
+
 // split: 1 two warps per instance, 2 one thread with the state in shared
 // memory, -1 one thread re-deriving it, 0 the library's choice; lanes: lanes
 // per instance for the lane-parallel kernel (0: not asked for)
@@ -156,10 +197,15 @@ int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const
         // n = 32, B = 1024: 13.6 / 12.7 / 10.4 / 12.5, B = 4096: 13.6 / 12.7 /
         // 11.3 / 13.5, B = 8192: 13.9 / 13.5 / 19.1 / 14.2; n = 64, B = 8192:
         // 26.8 / 45.0 / 57.7 / 25.8; n = 100, B = 8192: 45.8 / - / 201 / 41.9.
+        // Two warps with the state in shared memory (rnea_vjp_duo.cuh; B = 1024 /
+        // 4096 / 8192): n = 32: 11.6 / 12.1 / 13.4 against 12.6 / 12.7 / 13.5 for
+        // the shared state and 10.3 / 11.4 / 18.8 for 8 lanes; n = 64: 20.7 /
+        // 21.1 / 40.2 (one block per SM) against 22.3 / 23.1 / 24.6 for two warps.
         if (split == 0 && lanes == 0) {
             const int n = m->n;
             if (n > 16 && n <= 32 && B <= 4096) lanes = 8;
             else if (n <= 32 && B <= 8192) split = 2;
+            else if (n > 32 && n <= 64 && B <= 4096) split = 3;
             else if (n > 32 && B <= 8192) split = 1;
         }
         if (lanes > 0)
@@ -176,6 +222,11 @@ int launch_vjp_dh(const rd_model *m, int B, const void *q, const void *qd, const
             if (m->n <= 32)
                 return launch_vjp_pair_k<32, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
             return launch_vjp_pair_k<128, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
+        }
+        if (split == 3) {
+            if (m->n <= 32)
+                return launch_vjp_duo_k<32, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
+            return launch_vjp_duo_k<64, TRIG>(m, B, q, qd, qdd, w, gq, gqd, gqdd, base18, s);
         }
     }
     // small batches: 32-thread blocks spread the few warps over more SMs
@@ -198,9 +249,10 @@ int launch_vjp_any(const rd_model *m, int B, const void *q, const void *qd, cons
     const bool dh = !joint_frames && m->n % 4 == 0 && m->n <= 128 && vjp_aligned16(q) &&
                     vjp_aligned16(qd) && vjp_aligned16(qdd) && vjp_aligned16(w) &&
                     vjp_aligned16(gq) && vjp_aligned16(gqd) && vjp_aligned16(gqdd);
-    if (split == 2 && (!dh || MODE != kVjpRecompute))
-        return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_SHARED_STATE needs recompute (or AUTO) "
-                                   "mode and 16-byte aligned rows");
+    if ((split == 2 || split == 3) && (!dh || MODE != kVjpRecompute))
+        return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_SHARED_STATE and "
+                                   "RD_VJP_FLAG_TWO_WARPS_SHARED need recompute (or AUTO) mode and "
+                                   "16-byte aligned rows");
     if (lanes && (!dh || sizeof(T) != 4 || MODE != kVjpRecompute))
         return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_LANES needs FP32 data in recompute mode, "
                                    "n %% 4 == 0, n <= 128 and 16-byte aligned rows");
@@ -226,10 +278,20 @@ int vjp_dispatch(const rd_model *m, int B, const void *q, const void *qd, const 
     int split = (mode & RD_VJP_FLAG_TWO_WARPS) ? 1 : (mode & RD_VJP_FLAG_ONE_THREAD) ? -1 : 0;
     if (mode & RD_VJP_FLAG_SHARED_STATE) {
         if (split != 0 || sizeof(T) != 4 || m->n > 64 || m->n % 4 != 0 ||
-            (mode & (RD_VJP_FLAG_LANES | RD_VJP_FLAG_LANES4 | RD_VJP_FLAG_JOINT_FRAMES)))
+            (mode & (RD_VJP_FLAG_LANES | RD_VJP_FLAG_LANES4 | RD_VJP_FLAG_JOINT_FRAMES |
+                     RD_VJP_FLAG_TWO_WARPS_SHARED)))
             return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_SHARED_STATE needs FP32, n %% 4 == 0, "
                                        "n <= 64 and no other mapping flag");
         split = 2;
+    }
+    if (mode & RD_VJP_FLAG_TWO_WARPS_SHARED) {
+        if (split != 0 || sizeof(T) != 4 || m->n > 64 || m->n % 4 != 0 ||
+            (mode & (RD_VJP_FLAG_LANES | RD_VJP_FLAG_LANES4 | RD_VJP_FLAG_JOINT_FRAMES)) ||
+            (mode & 0xff) == RD_VJP_STORE)
+            return rd_fail(RD_ERR_ARG, "rnea_vjp: RD_VJP_FLAG_TWO_WARPS_SHARED needs FP32, "
+                                       "n %% 4 == 0, n <= 64, no workspace mode and no other "
+                                       "mapping flag");
+        split = 3;
     }
     const int lanes = (mode & RD_VJP_FLAG_LANES4) ? 4 : (mode & RD_VJP_FLAG_LANES) ? 8 : 0;
     if (lanes && (split != 0 || joint_frames))

@@ -379,3 +379,96 @@ def test_vjp_shared_state_rejects_what_it_does_not_cover(cuda_lib):
     with pytest.raises(cuda_lib.RdError):
         cuda_lib.rnea_vjp(m8, z, z, z, z, mode=cuda_lib.RD_VJP_RECOMPUTE | flag |
                           cuda_lib.RD_VJP_FLAG_LANES)
+
+
+# ---- two warps per 32 instances with the state in shared memory
+# (RD_VJP_FLAG_TWO_WARPS_SHARED): motion, wrench and dVbar on one warp, the
+# adjoint weight and Vbar (with its own dVbar carry) on the other
+
+def _duo(rd):
+    return rd.RD_VJP_RECOMPUTE | rd.RD_VJP_FLAG_TWO_WARPS_SHARED
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 36, 64])
+@pytest.mark.parametrize("B", [1, 31, 33, 300])
+def test_vjp_duo_matches_complex_step(cuda_lib, n, B):
+    g, ref, _, _ = run(cuda_lib, n, B, "float32", _duo(cuda_lib), seed=29)
+    assert grad_err(g, ref) <= TOL["float32"], f"n={n} B={B}"
+
+
+def test_vjp_duo_base_motion_wrench_and_fast_trig(cuda_lib):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    g, ref, _, _ = run(cuda_lib, 12, 70, "float32", _duo(cuda_lib), base=base, seed=23)
+    assert grad_err(g, ref) <= TOL["float32"]
+    g, ref, _, _ = run(cuda_lib, 32, 200, "float32", _duo(cuda_lib) | cuda_lib.RD_FLAG_FAST_TRIG,
+                       seed=17)
+    assert grad_err(g, ref) <= TOL["float32"]
+
+
+def test_vjp_duo_workload_agrees_with_shared_state(cuda_lib):
+    """n = 32, B = 8192 (the adjoint workload): the same formulas as the
+    one-thread kernel with its state in shared memory, split over two warps;
+    gqdd and the terms agree to the last bits (the two warps evaluate the same
+    operations, the compiler may contract a sum differently), and a sample
+    matches the oracle."""
+    import torch
+
+    n, B = 32, 8192
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=5003, kinds=("q", "qd", "qdd", "w"))
+    x = [torch.from_numpy(st[k]).float().cuda() for k in ("q", "qd", "qdd", "w")]
+    model = cuda_lib.Model(ch)
+    g = cuda_lib.rnea_vjp(model, *x, mode=_duo(cuda_lib))
+    h = cuda_lib.rnea_vjp(model, *x, mode=cuda_lib.RD_VJP_RECOMPUTE |
+                          cuda_lib.RD_VJP_FLAG_SHARED_STATE)
+    torch.cuda.synchronize()
+    for a, b in zip(g, h):
+        scale = float(b.abs().max())
+        assert float((a - b).abs().max()) <= 1e-5 * scale
+    idx = np.arange(0, B, 64)
+    ref = oracle.rnea_grad(ch, *(a.cpu().double().numpy()[idx] for a in x))
+    assert grad_err([a.cpu().numpy()[idx] for a in g], ref) <= TOL["float32"]
+
+
+def test_vjp_duo_rejects_what_it_does_not_cover(cuda_lib):
+    import torch
+
+    flag = cuda_lib.RD_VJP_FLAG_TWO_WARPS_SHARED
+    m100 = cuda_lib.Model(chaingen.make_chain(100))
+    x = torch.zeros((4, 100), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(m100, x, x, x, x, mode=cuda_lib.RD_VJP_RECOMPUTE | flag)
+    m8 = cuda_lib.Model(chaingen.make_chain(8))
+    z = torch.zeros((4, 8), device="cuda")
+    for other in (cuda_lib.RD_VJP_FLAG_LANES, cuda_lib.RD_VJP_FLAG_TWO_WARPS,
+                  cuda_lib.RD_VJP_FLAG_ONE_THREAD, cuda_lib.RD_VJP_FLAG_SHARED_STATE,
+                  cuda_lib.RD_VJP_FLAG_JOINT_FRAMES):
+        with pytest.raises(cuda_lib.RdError):
+            cuda_lib.rnea_vjp(m8, z, z, z, z, mode=cuda_lib.RD_VJP_RECOMPUTE | flag | other)
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(m8, z, z, z, z, mode=cuda_lib.RD_VJP_STORE | flag)
+    m7 = cuda_lib.Model(chaingen.make_chain(7))
+    y = torch.zeros((4, 7), device="cuda")
+    with pytest.raises(cuda_lib.RdError):
+        cuda_lib.rnea_vjp(m7, y, y, y, y, mode=cuda_lib.RD_VJP_RECOMPUTE | flag)
+
+
+@pytest.mark.parametrize("n,B,flag", [(48, 2048, "duo"), (64, 4096, "duo"), (64, 8192, "pair"),
+                                      (32, 8192, "shared")])
+def test_vjp_auto_picks_the_measured_mapping(cuda_lib, n, B, flag):
+    """FP32 recompute without a mapping flag follows the measured crossover:
+    the AUTO result equals the chosen mapping's bit for bit."""
+    import torch
+
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED)
+    st = chaingen.make_states(B, n, seed=41, kinds=("q", "qd", "qdd", "w"))
+    x = [torch.from_numpy(st[k]).float().cuda() for k in ("q", "qd", "qdd", "w")]
+    model = cuda_lib.Model(ch)
+    rec = cuda_lib.RD_VJP_RECOMPUTE
+    pick = {"duo": cuda_lib.RD_VJP_FLAG_TWO_WARPS_SHARED, "pair": cuda_lib.RD_VJP_FLAG_TWO_WARPS,
+            "shared": cuda_lib.RD_VJP_FLAG_SHARED_STATE}[flag]
+    a = cuda_lib.rnea_vjp(model, *x, mode=rec)
+    b = cuda_lib.rnea_vjp(model, *x, mode=rec | pick)
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
