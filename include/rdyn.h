@@ -182,6 +182,11 @@ enum rd_variant {
 /* OR-able tuning field for RD_VARIANT_SERIAL_HYBRID: links whose state is kept
  * (a multiple of 4, at most RD_MAX_LINKS; 0 = library default). */
 #define RD_TUNE_STORED_LINKS(links) (((links) / 4) << 20)
+/* OR-able tuning field for RD_VARIANT_SERIAL_DH (FP32, n <= 32, 32-thread
+ * blocks): of the stored links, the first `links` (4, 8, 12 or 16) keep their
+ * state in registers instead of shared memory, so that more blocks fit per SM.
+ * Needs at least that many stored links (RD_TUNE_STORED_LINKS). */
+#define RD_TUNE_REG_STATE_LINKS(links) (((links) / 4) << 28)
 
 #define RD_MAX_LINKS 128
 
@@ -535,6 +540,10 @@ int rd_joint_trig_df(const double *x, double *s, double *c, int count, void *str
 #define RD_RNEA_KERNEL_DH_TMEM 0x208
 #define RD_RNEA_KERNEL_DH_HOST 0x209 /* rnea_batch_host reading mapped host arrays */
 int rd_rnea_last_config(int *kernel, int *block, int *stored_links);
+/* Of those stored links, how many the last launch kept in registers
+ * (RD_TUNE_REG_STATE_LINKS, or the library's choice; 0 for every other kernel).
+ * Errors: RD_ERR_ARG (null output). */
+int rd_rnea_last_register_links(int *register_links);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *rd_last_error(void);

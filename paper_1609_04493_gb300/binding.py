@@ -137,6 +137,8 @@ def load(build_if_missing=True):
         IP = ctypes.POINTER(ctypes.c_int)
         lib.rd_rnea_last_config.argtypes = [IP, IP, IP]
         lib.rd_rnea_last_config.restype = I
+        lib.rd_rnea_last_register_links.argtypes = [IP]
+        lib.rd_rnea_last_register_links.restype = I
         _lib = lib
         return lib
 
@@ -172,6 +174,15 @@ def rnea_last_config():
     k, b, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib.rd_rnea_last_config(ctypes.byref(k), ctypes.byref(b), ctypes.byref(s)))
     return k.value, b.value, s.value
+
+
+def rnea_last_register_links():
+    """Of the stored links of this thread's last rnea_batch launch, how many the
+    kernel kept in registers (rd_rnea_last_register_links)."""
+    lib = load()
+    r = ctypes.c_int()
+    _check(lib.rd_rnea_last_register_links(ctypes.byref(r)))
+    return r.value
 
 
 def joint_trig(x, fast=False, stream=None):
@@ -467,6 +478,10 @@ RD_REQ_FD = 1
 RD_SCHED_PERSISTENT = 0
 RD_SCHED_PER_GROUP = 1
 RD_FLEET_FP64_UPDATE = 0x10
+
+
+def RD_TUNE_REG_STATE_LINKS(links):
+    return (int(links) // 4) << 28
 
 
 def RD_FLEET_TUNE(log2_threads, ctas_per_sm):

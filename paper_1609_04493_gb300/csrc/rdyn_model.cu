@@ -37,6 +37,13 @@ extern "C" int rd_rnea_last_config(int *kernel, int *block, int *stored_links)
     return RD_OK;
 }
 
+extern "C" int rd_rnea_last_register_links(int *register_links)
+{
+    if (!register_links) return rd_fail(RD_ERR_ARG, "rd_rnea_last_register_links: null output");
+    *register_links = g_rd_last_rnea.register_links;
+    return RD_OK;
+}
+
 int rd_fail(int code, const char *fmt, ...)
 {
     char buf[512];

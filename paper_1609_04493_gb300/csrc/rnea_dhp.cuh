@@ -91,25 +91,35 @@ __device__ __forceinline__ void read_chunk2(const unsigned char *ring, int slot,
         }
 }
 
+// RL: how many of the K stored links (the first ones) keep their state in
+// registers instead of shared memory
 template <typename T>
-__host__ __device__ constexpr size_t dhp_smem_per_thread(int n, int K)
+__host__ __device__ constexpr size_t dhp_smem_per_thread(int n, int K, int RL = 0)
 {
-    return (size_t)stage_bytes_per_thread<T>() + (size_t)K * 8 * sizeof(T) +
+    return (size_t)stage_bytes_per_thread<T>() + (size_t)(K - RL) * 8 * sizeof(T) +
            (size_t)(n - K) * 2 * sizeof(T);
 }
 
-// Shared memory: the staging ring, then K links x 8 scalars, then (n - K)
-// links x 2 scalars, each interleaved over the block's threads.
-template <typename T, int NMAX, int BLOCK, int TRIG>
+// Shared memory: the staging ring, then links RL..K-1 x 8 scalars, then
+// (n - K) links x 2 scalars, each interleaved over the block's threads. The
+// state of links 0..RL-1 (RL a multiple of 4, K >= RL) stays in registers: the
+// chunks that hold them run as unrolled copies of the loop body, first in the
+// forward sweep and last in the backward sweep, so every register index is a
+// compile-time constant. With less shared memory per block more blocks are
+// resident.
+template <typename T, int NMAX, int BLOCK, int TRIG, int RL = 0>
 __global__ void __launch_bounds__(BLOCK)
 rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K, int B,
                 const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ qdd,
                 T *__restrict__ tau, BaseParams<T> base)
 {
+    static_assert(RL % 4 == 0 && RL >= 0 && RL <= 16, "register links: 0, 4, 8, 12 or 16");
+    constexpr int kRegChunks = RL / 4;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *ring = smem;
     unsigned char *stf = ring + (size_t)stage_bytes_per_thread<T>() * BLOCK;
-    unsigned char *stc = stf + (size_t)K * 8 * sizeof(T) * BLOCK;
+    unsigned char *stc = stf + (size_t)(K - RL) * 8 * sizeof(T) * BLOCK;
+    LinkState<T> rs[kRegChunks > 0 ? RL : 1];
     const T *sc = pc.c;
 
     const int tid = threadIdx.x;
@@ -133,7 +143,31 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
         if (k < nchunks) stage_chunk<T, BLOCK>(ring, k, tid, qr, qdr, qddr, 4 * k);
         __pipeline_commit();
     }
-    for (int kc = 0; kc < nchunks; ++kc) {
+    // one stored link of the forward sweep: motion, bias wrench, cos, sin
+    auto forward_stored = [&](int i, T qi, T qdi, T qddi) -> LinkState<T> {
+        DhLink<T> L;
+        load_dh(sc + i * kDhConsts, L);
+        T s, c;
+        dh_trig<T, TRIG>(qi + L.th0, &s, &c);
+        x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, qdi, qddi, x);
+        LinkState<T> ls;
+        ls.Fh = bias_wrench(L.m, L.c, L.I, x);
+        ls.c = c;
+        ls.s = s;
+        return ls;
+    };
+    // the chunks whose state stays in registers
+#pragma unroll
+    for (int kc = 0; kc < kRegChunks; ++kc) {
+        const int ahead = kc + kStages - 1;
+        if (ahead < nchunks) stage_chunk<T, BLOCK>(ring, ahead % kStages, tid, qr, qdr, qddr, 4 * ahead);
+        __pipeline_commit();
+        __pipeline_wait_prior(kStages - 1);
+        read_chunk<T, BLOCK>(ring, kc % kStages, tid, cq, cqd, cqdd);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) rs[4 * kc + j] = forward_stored(4 * kc + j, cq.v[j], cqd.v[j], cqdd.v[j]);
+    }
+    for (int kc = kRegChunks; kc < nchunks; ++kc) {
         const int i0 = 4 * kc;
         const int ahead = kc + kStages - 1;
         if (ahead < nchunks) stage_chunk<T, BLOCK>(ring, ahead % kStages, tid, qr, qdr, qddr, 4 * ahead);
@@ -144,16 +178,7 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int i = i0 + j;
-                DhLink<T> L;
-                load_dh(sc + i * kDhConsts, L);
-                T s, c;
-                dh_trig<T, TRIG>(cq.v[j] + L.th0, &s, &c);
-                x = dh_forward(dh_rot(L.ca, L.sa, c, s), L.b, cqd.v[j], cqdd.v[j], x);
-                LinkState<T> ls;
-                ls.Fh = bias_wrench(L.m, L.c, L.I, x);
-                ls.c = c;
-                ls.s = s;
-                put_state<T>(stf, i, tid, BLOCK, ls);
+                put_state<T>(stf, i - RL, tid, BLOCK, forward_stored(i, cq.v[j], cqd.v[j], cqdd.v[j]));
             }
         } else {
 #pragma unroll
@@ -214,28 +239,38 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
         }
         st_chunk<T, true>(taur, i0, n, ct);
     }
-    // ---- then the links with full state
-    for (int kb = nrc; kb < nchunks; ++kb) {
+    // ---- then the links with full state: shared memory, then registers
+    auto backward_stored = [&](int i, const LinkState<T> &ls) -> T {
+        if (i == n - 1) {
+            F.f = add3(F.f, ls.Fh.f);
+            F.n = add3(F.n, ls.Fh.n);
+        } else {
+            F = dh_carry(Rn, bn, F, ls.Fh);
+        }
+        DhXf<T> X;
+        load_dh_xf(sc + i * kDhConsts, X);
+        Rn = dh_rot(X.ca, X.sa, ls.c, ls.s);
+        bn = X.b;
+        return F.n.z;
+    };
+    for (int kb = nrc; kb < nchunks - kRegChunks; ++kb) {
         const int i0 = last0 - 4 * kb;
         Chunk<T> ct;
 #pragma unroll
         for (int j = 3; j >= 0; --j) {
             const int i = i0 + j;
             LinkState<T> ls;
-            get_state<T>(stf, i, tid, BLOCK, ls);
-            if (i == n - 1) {
-                F.f = add3(F.f, ls.Fh.f);
-                F.n = add3(F.n, ls.Fh.n);
-            } else {
-                F = dh_carry(Rn, bn, F, ls.Fh);
-            }
-            DhXf<T> X;
-            load_dh_xf(sc + i * kDhConsts, X);
-            Rn = dh_rot(X.ca, X.sa, ls.c, ls.s);
-            bn = X.b;
-            ct.v[j] = F.n.z;
+            get_state<T>(stf, i - RL, tid, BLOCK, ls);
+            ct.v[j] = backward_stored(i, ls);
         }
         st_chunk<T, true>(taur, i0, n, ct);
+    }
+#pragma unroll
+    for (int kc = kRegChunks - 1; kc >= 0; --kc) {
+        Chunk<T> ct;
+#pragma unroll
+        for (int j = 3; j >= 0; --j) ct.v[j] = backward_stored(4 * kc + j, rs[4 * kc + j]);
+        st_chunk<T, true>(taur, 4 * kc, n, ct);
     }
 }
 

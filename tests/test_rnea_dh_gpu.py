@@ -300,3 +300,70 @@ def test_tmem_state_rejects_unsupported_rows(cuda_lib):
     z = torch.zeros((64, 36), dtype=torch.float32, device="cuda")
     with pytest.raises(cuda_lib.RdError, match="TMEM"):
         cuda_lib.rnea(model, z, z, z, variant=cuda_lib.RD_VARIANT_SERIAL_DH_TMEM)
+
+
+# ---- the first stored links' state in registers (RD_TUNE_REG_STATE_LINKS)
+
+@pytest.mark.parametrize("n,K,R", [(4, 4, 4), (8, 8, 4), (8, 8, 8), (12, 12, 4), (16, 16, 8),
+                                   (20, 20, 4), (20, 12, 8), (24, 24, 8), (28, 28, 4),
+                                   (32, 32, 8), (32, 24, 12), (32, 32, 16), (32, 16, 16)])
+def test_register_state_parity_and_bits(cuda_lib, n, K, R):
+    """Against the oracle, and bit for bit against the same K held in shared
+    memory (the arithmetic is the same; only where the state sits changes)."""
+    torch = _torch()
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    v = cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(32) | cuda_lib.RD_TUNE_STORED_LINKS(K)
+    tau, ref = run(cuda_lib, ch, 1000, "float32", v | cuda_lib.RD_TUNE_REG_STATE_LINKS(R))
+    assert oracle.rel_err(tau, ref) <= TOL["float32"], f"n={n} K={K} R={R}"
+    assert cuda_lib.rnea_last_register_links() == R
+    tau0, _ = run(cuda_lib, ch, 1000, "float32", v)
+    assert np.array_equal(tau, tau0)
+
+
+@pytest.mark.parametrize("B", [1, 31, 33, 4097])
+def test_register_state_ragged_batches_base_and_fast_trig(cuda_lib, B):
+    base = np.array([0.2, -0.1, 0.3, 0.5, -0.4, 0.25, 0.3, 1.1, 9.81, -0.2, 0.4, 0.1,
+                     2.0, -1.0, 0.5, 0.3, 0.2, -0.6])
+    ch = chaingen.make_chain(32, seed=chaingen.BASE_SEED + 1)
+    v = (cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(32) |
+         cuda_lib.RD_TUNE_STORED_LINKS(32) | cuda_lib.RD_TUNE_REG_STATE_LINKS(8))
+    tau, ref = run(cuda_lib, ch, B, "float32", v, base=base)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+    tau, ref = run(cuda_lib, ch, B, "float32", v | cuda_lib.RD_FLAG_FAST_TRIG)
+    assert oracle.rel_err(tau, ref) <= TOL["float32"]
+
+
+@pytest.mark.parametrize("n,B,K,R", [(32, 65536, 32, 8), (32, 16384, 32, 4), (32, 32768, 32, 8),
+                                     (20, 65536, 20, 4), (24, 65536, 24, 8), (8, 65536, 8, 8)])
+def test_auto_register_state_choice(cuda_lib, n, B, K, R):
+    """AUTO for FP32 n <= 32 (past the scan kernel's batches) stores every link
+    and keeps the measured number of them in registers."""
+    torch = _torch()
+    model = cuda_lib.Model(chaingen.make_chain(n))
+    z = torch.zeros((B, n), dtype=torch.float32, device="cuda")
+    cuda_lib.rnea(model, z, z, z)
+    kern, block, stored = cuda_lib.rnea_last_config()
+    assert kern == cuda_lib.RD_RNEA_KERNEL_DH_PARAM and block == 32
+    assert (stored, cuda_lib.rnea_last_register_links()) == (K, R)
+
+
+def test_register_state_rejections(cuda_lib):
+    torch = _torch()
+    m48 = cuda_lib.Model(chaingen.make_chain(48))
+    x48 = torch.zeros((64, 48), device="cuda")
+    base_v = cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(32)
+    with pytest.raises(cuda_lib.RdError):  # n > 32
+        cuda_lib.rnea(m48, x48, x48, x48, variant=base_v | cuda_lib.RD_TUNE_STORED_LINKS(48) |
+                      cuda_lib.RD_TUNE_REG_STATE_LINKS(8))
+    m16 = cuda_lib.Model(chaingen.make_chain(16))
+    x16 = torch.zeros((64, 16), device="cuda")
+    for v in (base_v | cuda_lib.RD_TUNE_STORED_LINKS(4) | cuda_lib.RD_TUNE_REG_STATE_LINKS(8),
+              cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(64) |
+              cuda_lib.RD_TUNE_STORED_LINKS(16) | cuda_lib.RD_TUNE_REG_STATE_LINKS(8),
+              cuda_lib.RD_VARIANT_SERIAL_DH_RECOMPUTE | cuda_lib.RD_TUNE_REG_STATE_LINKS(8)):
+        with pytest.raises(cuda_lib.RdError):
+            cuda_lib.rnea(m16, x16, x16, x16, variant=v)
+    x16d = torch.zeros((64, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(cuda_lib.RdError):  # FP64
+        cuda_lib.rnea(m16, x16d, x16d, x16d, variant=base_v | cuda_lib.RD_TUNE_STORED_LINKS(16) |
+                      cuda_lib.RD_TUNE_REG_STATE_LINKS(8))
