@@ -631,7 +631,7 @@ def run_ours(args):
     t32 = max_over_ranks(dist, timed_graph(torch, g32, dist, sampler))
     value = world * BATCH * K / t32
     kern_id, kern_block, kern_stored = rd.rnea_last_config()
-    kern_reg = rd.rnea_last_register_links()
+    kern_reg, kern_ring = rd.rnea_last_state_layout()
     del g32, gw
 
     raw = {}
@@ -703,7 +703,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (one FP32 RNEA launch per step)
     if kern_id == rd.RD_RNEA_KERNEL_DH_PARAM:
-        kname = f"rnea_dhp_kernel<float,{kern_block}>,K={kern_stored},R={kern_reg}"
+        kname = f"rnea_dhp_kernel<float,{kern_block}>,K={kern_stored},R={kern_reg},S={kern_ring}"
         exec_fpl = dh_param_flops(N_LINKS, kern_stored) / N_LINKS
     else:
         kname = f"rnea family {kern_id:#x},{kern_block}"

@@ -187,6 +187,10 @@ enum rd_variant {
  * state in registers instead of shared memory, so that more blocks fit per SM.
  * Needs at least that many stored links (RD_TUNE_STORED_LINKS). */
 #define RD_TUNE_REG_STATE_LINKS(links) (((links) / 4) << 28)
+/* OR-able tuning flag for RD_VARIANT_SERIAL_DH (the same rows as
+ * RD_TUNE_REG_STATE_LINKS): stage the joint values through a ring of two
+ * chunks instead of three, 48 bytes less shared memory per thread. */
+#define RD_TUNE_TWO_STAGE_RING 0x8000
 
 #define RD_MAX_LINKS 128
 
@@ -540,10 +544,12 @@ int rd_joint_trig_df(const double *x, double *s, double *c, int count, void *str
 #define RD_RNEA_KERNEL_DH_TMEM 0x208
 #define RD_RNEA_KERNEL_DH_HOST 0x209 /* rnea_batch_host reading mapped host arrays */
 int rd_rnea_last_config(int *kernel, int *block, int *stored_links);
-/* Of those stored links, how many the last launch kept in registers
- * (RD_TUNE_REG_STATE_LINKS, or the library's choice; 0 for every other kernel).
- * Errors: RD_ERR_ARG (null output). */
-int rd_rnea_last_register_links(int *register_links);
+/* Where the last launch of the common-normal kernel with stored state kept it:
+ * how many of the stored links in registers (RD_TUNE_REG_STATE_LINKS, or the
+ * library's choice), and how many chunks of joint values its staging ring
+ * held (3, or 2 with RD_TUNE_TWO_STAGE_RING or the library's choice); both 0
+ * after any other kernel. Errors: RD_ERR_ARG (null output). */
+int rd_rnea_last_state_layout(int *register_links, int *ring_chunks);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *rd_last_error(void);

@@ -137,8 +137,8 @@ def load(build_if_missing=True):
         IP = ctypes.POINTER(ctypes.c_int)
         lib.rd_rnea_last_config.argtypes = [IP, IP, IP]
         lib.rd_rnea_last_config.restype = I
-        lib.rd_rnea_last_register_links.argtypes = [IP]
-        lib.rd_rnea_last_register_links.restype = I
+        lib.rd_rnea_last_state_layout.argtypes = [IP, IP]
+        lib.rd_rnea_last_state_layout.restype = I
         _lib = lib
         return lib
 
@@ -176,13 +176,19 @@ def rnea_last_config():
     return k.value, b.value, s.value
 
 
+def rnea_last_state_layout():
+    """(register links, ring chunks) of this thread's last rnea_batch launch of
+    the stored-state common-normal kernel (rd_rnea_last_state_layout)."""
+    lib = load()
+    r, c = ctypes.c_int(), ctypes.c_int()
+    _check(lib.rd_rnea_last_state_layout(ctypes.byref(r), ctypes.byref(c)))
+    return r.value, c.value
+
+
 def rnea_last_register_links():
     """Of the stored links of this thread's last rnea_batch launch, how many the
-    kernel kept in registers (rd_rnea_last_register_links)."""
-    lib = load()
-    r = ctypes.c_int()
-    _check(lib.rd_rnea_last_register_links(ctypes.byref(r)))
-    return r.value
+    kernel kept in registers."""
+    return rnea_last_state_layout()[0]
 
 
 def joint_trig(x, fast=False, stream=None):
@@ -478,6 +484,9 @@ RD_REQ_FD = 1
 RD_SCHED_PERSISTENT = 0
 RD_SCHED_PER_GROUP = 1
 RD_FLEET_FP64_UPDATE = 0x10
+
+
+RD_TUNE_TWO_STAGE_RING = 0x8000
 
 
 def RD_TUNE_REG_STATE_LINKS(links):

@@ -42,15 +42,17 @@ extern thread_local std::string g_rd_error;
 // Kernel, block size and stored links of the calling thread's last rnea_batch
 // launch (rd_rnea_last_config).
 struct RdLaunchConfig {
-    int kernel = 0, block = 0, stored_links = 0, register_links = 0;
+    int kernel = 0, block = 0, stored_links = 0, register_links = 0, ring_chunks = 0;
 };
 extern thread_local RdLaunchConfig g_rd_last_rnea;
-inline void rd_note_rnea(int kernel, int block, int stored, int register_links = 0)
+inline void rd_note_rnea(int kernel, int block, int stored, int register_links = 0,
+                         int ring_chunks = 0)
 {
     g_rd_last_rnea.kernel = kernel;
     g_rd_last_rnea.block = block;
     g_rd_last_rnea.stored_links = stored;
     g_rd_last_rnea.register_links = register_links;
+    g_rd_last_rnea.ring_chunks = ring_chunks;
 }
 int rd_fail(int code, const char *fmt, ...);
 int rd_cuda_fail(cudaError_t e, const char *what);
@@ -61,10 +63,10 @@ int rd_build_dh(int n, const std::vector<double> &c64, std::vector<double> &dh64
 void rd_build_aba64(int n, const std::vector<double> &dh64, std::vector<double> &out);
 int rd_rnea_dh_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
-                   int kfull, int tmem, int reg_links, cudaStream_t s);
+                   int kfull, int tmem, int reg_links, int stages, cudaStream_t s);
 int rd_rnea_dh_f64(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
                    void *tau, const double *base18, int stored, int block, int fast,
-                   int kfull, int tmem, int reg_links, cudaStream_t s);
+                   int kfull, int tmem, int reg_links, int stages, cudaStream_t s);
 // FP32 inverse dynamics reading and writing mapped pinned host arrays (device
 // addresses), n % 4 == 0, n <= 64, 16-byte aligned
 int rd_rnea_dhz_f32(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,

@@ -37,10 +37,12 @@ extern "C" int rd_rnea_last_config(int *kernel, int *block, int *stored_links)
     return RD_OK;
 }
 
-extern "C" int rd_rnea_last_register_links(int *register_links)
+extern "C" int rd_rnea_last_state_layout(int *register_links, int *ring_chunks)
 {
-    if (!register_links) return rd_fail(RD_ERR_ARG, "rd_rnea_last_register_links: null output");
+    if (!register_links || !ring_chunks)
+        return rd_fail(RD_ERR_ARG, "rd_rnea_last_state_layout: null output");
     *register_links = g_rd_last_rnea.register_links;
+    *ring_chunks = g_rd_last_rnea.ring_chunks;
     return RD_OK;
 }
 

@@ -100,12 +100,12 @@ int launch_dh_mode(const rd_model *m, int block, int B, const void *q, const voi
     }
 }
 
-template <typename T, int NMAX, int BLOCK, int TRIG, int RL = 0>
+template <typename T, int NMAX, int BLOCK, int TRIG, int RL = 0, int STG = kStages>
 int launch_dhp_k(const rd_model *m, int K, int B, const void *q, const void *qd, const void *qdd,
                  void *tau, const BaseParams<T> &base, size_t smem, cudaStream_t stream)
 {
     static std::atomic<uint64_t> configured{0};
-    auto kern = rnea_dhp_kernel<T, NMAX, BLOCK, TRIG, RL>;
+    auto kern = rnea_dhp_kernel<T, NMAX, BLOCK, TRIG, RL, STG>;
     const uint64_t bit = 1ull << (m->device & 63);
     if (!(configured.load() & bit)) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -117,7 +117,7 @@ int launch_dhp_k(const rd_model *m, int K, int B, const void *q, const void *qd,
     for (int k = 0; k < m->n * kDhConsts; ++k) pc.c[k] = (T)m->host_dh64[k];
     for (int k = m->n * kDhConsts; k < NMAX * kDhConsts; ++k) pc.c[k] = T(0);
     const unsigned grid = (unsigned)((B + BLOCK - 1) / BLOCK);
-    rd_note_rnea(RD_RNEA_KERNEL_DH_PARAM, BLOCK, K, RL);
+    rd_note_rnea(RD_RNEA_KERNEL_DH_PARAM, BLOCK, K, RL, STG);
     kern<<<grid, BLOCK, smem, stream>>>(pc, m->n, K, B, static_cast<const T *>(q),
                                         static_cast<const T *>(qd), static_cast<const T *>(qdd),
                                         static_cast<T *>(tau), base);
@@ -188,42 +188,57 @@ bool dhp_eligible(const rd_model *m, const void *q, const void *qd, const void *
 }
 
 // Library default for FP32, n <= 32, 32-thread blocks: every link stored (K =
-// n), the first RL of them in registers. Measured on GB300 (µs, B = 65536,
-// AUTO before / chosen): n = 8: 5.68 / 5.15 (RL = 8, all in registers); 16:
-// 10.30 / 9.72 (8); 20: 13.50 / 12.16 (4); 24: 15.76 / 14.40 (8); 28: 18.54 /
-// 17.54 (4); 32: 21.78 / 20.21 (8); n = 32 at B = 4096 / 16384 / 32768 /
-// 262144: 6.63 / 7.31 / 11.19 / 70.42 against 6.29 (4) / 6.76 (4) / 10.32 (8)
-// / 68.90 (8). RL = 4 wins where n % 8 == 4 and where it already holds the
-// whole batch in one wave; RL = 8 otherwise (more blocks per SM, fewer waves);
-// 12 and 16 never led.
+// n), the first RL of them in registers, the joint values staged through a
+// ring of `stages` chunks. Measured on GB300 (µs at B = 65536; the previous
+// default of 24 or n links in shared memory / the choice): n = 8: 5.68 / 5.17
+// (RL = 8, all in registers); 12: 7.43 / 7.02 (8, two-chunk ring); 16: 10.30 /
+// 9.18 (8, two); 20: 13.50 / 11.63 (8, two); 24: 15.76 / 14.47 (8, three); 28:
+// 18.54 / 17.39 (8, two); 32: 21.78 / 20.25 (8, three; two: 20.96). Where RL =
+// 4 with the two-chunk ring holds the whole batch in half a wave it leads (n =
+// 16, B = 16384: 4.09 against 4.50 with 8; n = 32, B = 16384: 6.75 against
+// 7.14); near a full wave 8 does (n = 16, B = 65536: 9.18 against 9.39). 12 and
+// 16 register links never led: more blocks per SM, longer unrolled code.
 template <int TRIG>
-void dhp_default_kr(const rd_model *m, int B, int &K, int &RL)
+void dhp_default_kr(const rd_model *m, int B, int &K, int &RL, int &stages)
 {
     const int n = m->n;
     K = n;
+    stages = kStages;
     if (n <= 8) {
         RL = n;
         return;
     }
-    if (n % 8 == 4) {
-        RL = 4;
-        return;
-    }
     int per_sm = 0;
-    const size_t smem = dhp_smem_per_thread<float>(n, n, 4) * 32;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rnea_dhp_kernel<float, 32, 32, TRIG, 4>,
+    const size_t smem = dhp_smem_per_thread<float>(n, n, 4, 2) * 32;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rnea_dhp_kernel<float, 32, 32, TRIG, 4, 2>,
                                                   32, smem);
     const long long sms = dh_device_attr(m->device, cudaDevAttrMultiProcessorCount, 1);
-    RL = (long long)per_sm * sms >= (long long)(B + 31) / 32 ? 4 : 8;
+    if ((long long)per_sm * sms >= 2 * ((long long)(B + 31) / 32)) {
+        RL = 4;
+        stages = 2;
+        return;
+    }
+    RL = 8;
+    stages = (n == 24 || n == 32) ? kStages : 2;
 }
 
 // FP32, n <= 32, 32-thread blocks: the first RL of the K stored links keep
 // their state in registers (RL = 4, 8, 12 or 16; K >= RL)
 template <int TRIG>
-int launch_dhp_reg(const rd_model *m, int RL, int K, int B, const void *q, const void *qd,
-                   const void *qdd, void *tau, const BaseParams<float> &base, size_t smem,
-                   cudaStream_t s)
+int launch_dhp_reg(const rd_model *m, int RL, int stages, int K, int B, const void *q,
+                   const void *qd, const void *qdd, void *tau, const BaseParams<float> &base,
+                   size_t smem, cudaStream_t s)
 {
+    if (stages == 2) {
+        switch (RL) {
+        case 0: return launch_dhp_k<float, 32, 32, TRIG, 0, 2>(m, K, B, q, qd, qdd, tau, base, smem, s);
+        case 4: return launch_dhp_k<float, 32, 32, TRIG, 4, 2>(m, K, B, q, qd, qdd, tau, base, smem, s);
+        case 8: return launch_dhp_k<float, 32, 32, TRIG, 8, 2>(m, K, B, q, qd, qdd, tau, base, smem, s);
+        default: break;
+        }
+        return rd_fail(RD_ERR_ARG, "rnea_batch: the two-stage ring is built for 0, 4 or 8 register "
+                                   "links (%d asked)", RL);
+    }
     switch (RL) {
     case 4: return launch_dhp_k<float, 32, 32, TRIG, 4>(m, K, B, q, qd, qdd, tau, base, smem, s);
     case 8: return launch_dhp_k<float, 32, 32, TRIG, 8>(m, K, B, q, qd, qdd, tau, base, smem, s);
@@ -236,30 +251,31 @@ int launch_dhp_reg(const rd_model *m, int RL, int K, int B, const void *q, const
 template <typename T>
 int launch_dhp(const rd_model *m, int block, int K, int B, const void *q, const void *qd,
                const void *qdd, void *tau, const BaseParams<T> &base, bool fast, cudaStream_t s,
-               int RL = 0)
+               int RL = 0, int stages = kStages)
 {
     const int n = m->n;
     if constexpr (sizeof(T) == 4) {
-        if (K < 0 && RL == 0 && block == 32 && n <= 32) {
-            if (fast) dhp_default_kr<kTrigSfu>(m, B, K, RL);
-            else dhp_default_kr<kTrigPoly>(m, B, K, RL);
+        if (K < 0 && RL == 0 && stages == kStages && block == 32 && n <= 32) {
+            if (fast) dhp_default_kr<kTrigSfu>(m, B, K, RL, stages);
+            else dhp_default_kr<kTrigPoly>(m, B, K, RL, stages);
         }
     }
     if (K < 0) K = dhp_default_k<T>(m, B);
     K = K > n ? n : 4 * (K / 4);
-    if (RL) {
+    if (RL || stages != kStages) {
         if (sizeof(T) != 4 || n > 32 || block != 32 || RL % 4 || RL < 0 || RL > 16 || RL > K)
-            return rd_fail(RD_ERR_ARG, "rnea_batch: register state needs FP32, n <= 32, 32-thread "
-                                       "blocks and 4, 8, 12 or 16 links, at most the %d stored", K);
+            return rd_fail(RD_ERR_ARG, "rnea_batch: register state and the two-stage ring need "
+                                       "FP32, n <= 32, 32-thread blocks and 4, 8, 12 or 16 "
+                                       "register links, at most the %d stored", K);
     }
-    const size_t smem = dhp_smem_per_thread<T>(n, K, RL) * (size_t)block;
+    const size_t smem = dhp_smem_per_thread<T>(n, K, RL, stages) * (size_t)block;
     if (smem > (size_t)dh_smem_optin(m->device))
         return rd_fail(RD_ERR_ARG, "rnea_batch: state of %d links needs %zu bytes of shared "
                                    "memory, %d available", K, smem, dh_smem_optin(m->device));
     if constexpr (sizeof(T) == 4) {
-        if (RL)
-            return fast ? launch_dhp_reg<kTrigSfu>(m, RL, K, B, q, qd, qdd, tau, base, smem, s)
-                        : launch_dhp_reg<kTrigPoly>(m, RL, K, B, q, qd, qdd, tau, base, smem, s);
+        if (RL || stages != kStages)
+            return fast ? launch_dhp_reg<kTrigSfu>(m, RL, stages, K, B, q, qd, qdd, tau, base, smem, s)
+                        : launch_dhp_reg<kTrigPoly>(m, RL, stages, K, B, q, qd, qdd, tau, base, smem, s);
     }
     const bool sfu = sizeof(T) == 4 && fast;
     if (n <= 32)
@@ -373,7 +389,7 @@ inline int launch_dht(const rd_model *m, int K, int B, const void *q, const void
 template <typename T>
 int dh_launch(const rd_model *m, int B, const void *q, const void *qd, const void *qdd,
               void *tau, const double *base18, bool stored, int block, bool fast, int kfull,
-              bool tmem, int reg_links, cudaStream_t s)
+              bool tmem, int reg_links, int stages, cudaStream_t s)
 {
     double b[18];
     rd_convert_base_dh(m, base18, b);
@@ -391,12 +407,12 @@ int dh_launch(const rd_model *m, int B, const void *q, const void *qd, const voi
             return launch_dht(m, stored ? kfull : 0, B, q, qd, qdd, tau, base, fast, s);
         }
     }
-    if (reg_links && (!stored || tmem || !dhp_eligible<T>(m, q, qd, qdd, tau)))
+    if ((reg_links || stages != kStages) && (!stored || tmem || !dhp_eligible<T>(m, q, qd, qdd, tau)))
         return rd_fail(RD_ERR_ARG, "rnea_batch: register state is for the stored-state "
                                    "common-normal kernel (n %% 4 == 0, aligned rows)");
     if (dhp_eligible<T>(m, q, qd, qdd, tau))
         return launch_dhp<T>(m, block ? block : 32, stored ? kfull : 0, B, q, qd, qdd, tau, base,
-                             fast, s, reg_links);
+                             fast, s, reg_links, stages);
     if (stored) {
         if (!block)
             block = dh_smem<T>(m->n, 64, kStore, true) <= (size_t)dh_smem_optin(m->device) / 4 ? 64 : 32;

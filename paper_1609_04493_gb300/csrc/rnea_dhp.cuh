@@ -93,10 +93,11 @@ __device__ __forceinline__ void read_chunk2(const unsigned char *ring, int slot,
 
 // RL: how many of the K stored links (the first ones) keep their state in
 // registers instead of shared memory
+// STG: depth of the joint-value staging ring (3, or 2 to save shared memory)
 template <typename T>
-__host__ __device__ constexpr size_t dhp_smem_per_thread(int n, int K, int RL = 0)
+__host__ __device__ constexpr size_t dhp_smem_per_thread(int n, int K, int RL = 0, int STG = kStages)
 {
-    return (size_t)stage_bytes_per_thread<T>() + (size_t)(K - RL) * 8 * sizeof(T) +
+    return (size_t)STG * 3 * 4 * sizeof(T) + (size_t)(K - RL) * 8 * sizeof(T) +
            (size_t)(n - K) * 2 * sizeof(T);
 }
 
@@ -107,17 +108,18 @@ __host__ __device__ constexpr size_t dhp_smem_per_thread(int n, int K, int RL = 
 // forward sweep and last in the backward sweep, so every register index is a
 // compile-time constant. With less shared memory per block more blocks are
 // resident.
-template <typename T, int NMAX, int BLOCK, int TRIG, int RL = 0>
+template <typename T, int NMAX, int BLOCK, int TRIG, int RL = 0, int STG = kStages>
 __global__ void __launch_bounds__(BLOCK)
 rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K, int B,
                 const T *__restrict__ q, const T *__restrict__ qd, const T *__restrict__ qdd,
                 T *__restrict__ tau, BaseParams<T> base)
 {
     static_assert(RL % 4 == 0 && RL >= 0 && RL <= 16, "register links: 0, 4, 8, 12 or 16");
+    static_assert(STG == 2 || STG == 3, "staging ring of 2 or 3 chunks");
     constexpr int kRegChunks = RL / 4;
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *ring = smem;
-    unsigned char *stf = ring + (size_t)stage_bytes_per_thread<T>() * BLOCK;
+    unsigned char *stf = ring + (size_t)STG * 3 * 4 * sizeof(T) * BLOCK;
     unsigned char *stc = stf + (size_t)(K - RL) * 8 * sizeof(T) * BLOCK;
     LinkState<T> rs[kRegChunks > 0 ? RL : 1];
     const T *sc = pc.c;
@@ -139,7 +141,7 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
     const int nchunks = n / 4, kchunks = K / 4;
     Chunk<T> cq, cqd, cqdd;
 #pragma unroll
-    for (int k = 0; k < kStages - 1; ++k) {
+    for (int k = 0; k < STG - 1; ++k) {
         if (k < nchunks) stage_chunk<T, BLOCK>(ring, k, tid, qr, qdr, qddr, 4 * k);
         __pipeline_commit();
     }
@@ -159,21 +161,21 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
     // the chunks whose state stays in registers
 #pragma unroll
     for (int kc = 0; kc < kRegChunks; ++kc) {
-        const int ahead = kc + kStages - 1;
-        if (ahead < nchunks) stage_chunk<T, BLOCK>(ring, ahead % kStages, tid, qr, qdr, qddr, 4 * ahead);
+        const int ahead = kc + STG - 1;
+        if (ahead < nchunks) stage_chunk<T, BLOCK>(ring, ahead % STG, tid, qr, qdr, qddr, 4 * ahead);
         __pipeline_commit();
-        __pipeline_wait_prior(kStages - 1);
-        read_chunk<T, BLOCK>(ring, kc % kStages, tid, cq, cqd, cqdd);
+        __pipeline_wait_prior(STG - 1);
+        read_chunk<T, BLOCK>(ring, kc % STG, tid, cq, cqd, cqdd);
 #pragma unroll
         for (int j = 0; j < 4; ++j) rs[4 * kc + j] = forward_stored(4 * kc + j, cq.v[j], cqd.v[j], cqdd.v[j]);
     }
     for (int kc = kRegChunks; kc < nchunks; ++kc) {
         const int i0 = 4 * kc;
-        const int ahead = kc + kStages - 1;
-        if (ahead < nchunks) stage_chunk<T, BLOCK>(ring, ahead % kStages, tid, qr, qdr, qddr, 4 * ahead);
+        const int ahead = kc + STG - 1;
+        if (ahead < nchunks) stage_chunk<T, BLOCK>(ring, ahead % STG, tid, qr, qdr, qddr, 4 * ahead);
         __pipeline_commit();
-        __pipeline_wait_prior(kStages - 1);
-        read_chunk<T, BLOCK>(ring, kc % kStages, tid, cq, cqd, cqdd);
+        __pipeline_wait_prior(STG - 1);
+        read_chunk<T, BLOCK>(ring, kc % STG, tid, cq, cqd, cqdd);
         if (kc < kchunks) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -202,20 +204,20 @@ rnea_dhp_kernel(const __grid_constant__ DhParamConsts<T, NMAX> pc, int n, int K,
     V3<T> bn = mk3(T(0), T(0), T(0));
     const int last0 = n - 4;
     const int nrc = nchunks - kchunks;
-    // Forward chunk c was staged in slot c % kStages and is only overwritten by
-    // chunk c + kStages, so the ring still holds the last kStages chunks: the
-    // backward sweep reads those in place and stages older ones kStages - 1
+    // Forward chunk c was staged in slot c % STG and is only overwritten by
+    // chunk c + STG, so the ring still holds the last STG chunks: the
+    // backward sweep reads those in place and stages older ones STG - 1
     // steps ahead, each into the slot of the chunk read one step before.
     for (int kb = 0; kb < nrc; ++kb) {
         const int i0 = last0 - 4 * kb;
-        const int ahead = kb + kStages - 1;
-        if (ahead >= kStages && ahead < nrc) {
+        const int ahead = kb + STG - 1;
+        if (ahead >= STG && ahead < nrc) {
             const int c = nchunks - 1 - ahead;
-            stage_chunk2<T, BLOCK>(ring, c % kStages, tid, qdr, qddr, 4 * c);
+            stage_chunk2<T, BLOCK>(ring, c % STG, tid, qdr, qddr, 4 * c);
         }
         __pipeline_commit();
-        __pipeline_wait_prior(kStages - 1);
-        read_chunk2<T, BLOCK>(ring, (nchunks - 1 - kb) % kStages, tid, cqd, cqdd);
+        __pipeline_wait_prior(STG - 1);
+        read_chunk2<T, BLOCK>(ring, (nchunks - 1 - kb) % STG, tid, cqd, cqdd);
         Chunk<T> ct;
 #pragma unroll
         for (int j = 3; j >= 0; --j) {

@@ -296,6 +296,7 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
     if (block) block = 1 << block;
     const int reglinks = 4 * ((variant >> 20) & 0xff);  // RD_TUNE_REGLINKS / _STORED_LINKS
     const int regstate = 4 * ((variant >> 28) & 0x7);   // RD_TUNE_REG_STATE_LINKS
+    const int stages = (variant & RD_TUNE_TWO_STAGE_RING) ? 2 : kStages;
     variant &= 0xfff;
     const bool dhp_rows = sizeof(T) == 4 && n % 4 == 0 && n <= 128 && aligned16(q) &&
                           aligned16(qd) && aligned16(qdd) && aligned16(tau);
@@ -320,7 +321,7 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         // parameter, full state for the library's K (about 22% below the
         // joint-frame kernels at n = 16..100, B = 65536; see rnea_dh_launch.cuh)
         return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, 1, block, fast,
-                              reglinks ? reglinks : -1, 0, regstate, s);
+                              reglinks ? reglinks : -1, 0, regstate, stages, s);
     }
     if (variant == RD_VARIANT_AUTO) {
         // Sweep on GB300 at B = 65536 (modes x block sizes x stored links):
@@ -370,10 +371,10 @@ int dispatch(const rd_model *m, int B, const void *q, const void *qd, const void
         const int kfull = reglinks ? reglinks : -1;
         if constexpr (sizeof(T) == 4)
             return rd_rnea_dh_f32(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, tmem,
-                                  regstate, s);
+                                  regstate, stages, s);
         else
             return rd_rnea_dh_f64(m, B, q, qd, qdd, tau, base18, stored, block, fast, kfull, tmem,
-                                  regstate, s);
+                                  regstate, stages, s);
     }
     if (variant == RD_VARIANT_SERIAL_DF) {
         if constexpr (sizeof(T) == 8)

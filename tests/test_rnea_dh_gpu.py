@@ -315,7 +315,7 @@ def test_register_state_parity_and_bits(cuda_lib, n, K, R):
     v = cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(32) | cuda_lib.RD_TUNE_STORED_LINKS(K)
     tau, ref = run(cuda_lib, ch, 1000, "float32", v | cuda_lib.RD_TUNE_REG_STATE_LINKS(R))
     assert oracle.rel_err(tau, ref) <= TOL["float32"], f"n={n} K={K} R={R}"
-    assert cuda_lib.rnea_last_register_links() == R
+    assert cuda_lib.rnea_last_state_layout() == (R, 3)
     tau0, _ = run(cuda_lib, ch, 1000, "float32", v)
     assert np.array_equal(tau, tau0)
 
@@ -333,18 +333,35 @@ def test_register_state_ragged_batches_base_and_fast_trig(cuda_lib, B):
     assert oracle.rel_err(tau, ref) <= TOL["float32"]
 
 
-@pytest.mark.parametrize("n,B,K,R", [(32, 65536, 32, 8), (32, 16384, 32, 4), (32, 32768, 32, 8),
-                                     (20, 65536, 20, 4), (24, 65536, 24, 8), (8, 65536, 8, 8)])
-def test_auto_register_state_choice(cuda_lib, n, B, K, R):
-    """AUTO for FP32 n <= 32 (past the scan kernel's batches) stores every link
-    and keeps the measured number of them in registers."""
+@pytest.mark.parametrize("n,B,K,R,S", [(32, 65536, 32, 8, 3), (32, 16384, 32, 4, 2),
+                                       (24, 65536, 24, 8, 3), (20, 65536, 20, 8, 2),
+                                       (16, 65536, 16, 8, 2), (16, 16384, 16, 4, 2),
+                                       (8, 65536, 8, 8, 3)])
+def test_auto_register_state_choice(cuda_lib, n, B, K, R, S):
+    """AUTO for FP32 n <= 32 (past the scan kernel's batches) stores every link,
+    keeps the measured number of them in registers and stages through the
+    measured ring depth."""
     torch = _torch()
     model = cuda_lib.Model(chaingen.make_chain(n))
     z = torch.zeros((B, n), dtype=torch.float32, device="cuda")
     cuda_lib.rnea(model, z, z, z)
     kern, block, stored = cuda_lib.rnea_last_config()
     assert kern == cuda_lib.RD_RNEA_KERNEL_DH_PARAM and block == 32
-    assert (stored, cuda_lib.rnea_last_register_links()) == (K, R)
+    assert (stored,) + cuda_lib.rnea_last_state_layout() == (K, R, S)
+
+
+@pytest.mark.parametrize("n,R", [(12, 8), (16, 0), (16, 4), (20, 8), (32, 8)])
+def test_two_stage_ring_parity_and_bits(cuda_lib, n, R):
+    """RD_TUNE_TWO_STAGE_RING: the same arithmetic with a shallower staging
+    ring; bit for bit the three-chunk result, and the oracle's within the bar."""
+    ch = chaingen.make_chain(n, seed=chaingen.BASE_SEED + n)
+    v = (cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(32) |
+         cuda_lib.RD_TUNE_STORED_LINKS(n) | cuda_lib.RD_TUNE_REG_STATE_LINKS(R))
+    tau2, ref = run(cuda_lib, ch, 3000, "float32", v | cuda_lib.RD_TUNE_TWO_STAGE_RING)
+    assert cuda_lib.rnea_last_state_layout() == (R, 2)
+    assert oracle.rel_err(tau2, ref) <= TOL["float32"]
+    tau3, _ = run(cuda_lib, ch, 3000, "float32", v)
+    assert np.array_equal(tau2, tau3)
 
 
 def test_register_state_rejections(cuda_lib):
