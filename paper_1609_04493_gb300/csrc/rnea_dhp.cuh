@@ -65,8 +65,8 @@ __device__ __forceinline__ void stage_chunk2(unsigned char *ring, int slot, int 
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int h = 0; h < P; ++h)
-            __pipeline_memcpy_async(&r[((slot * 3 + a + 1) * P + h) * BLOCK + tid],
-                                    src[a] + i0 + h * (16 / (int)sizeof(T)), 16);
+            cp_async16_cg(&r[((slot * 3 + a + 1) * P + h) * BLOCK + tid],
+                          src[a] + i0 + h * (16 / (int)sizeof(T)));
 }
 
 template <typename T, int BLOCK>

@@ -269,6 +269,15 @@ __host__ __device__ constexpr int stage_bytes_per_thread()
     return kStages * 3 * 4 * (int)sizeof(T);
 }
 
+// 16 bytes from global into shared memory asynchronously, cached in L2 only:
+// the joint values are streamed once, so they need no L1 lines (the copy
+// joins the same commit groups as __pipeline_memcpy_async)
+__device__ __forceinline__ void cp_async16_cg(void *dst, const void *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
+}
+
 template <typename T, int BLOCK>
 __device__ __forceinline__ void stage_chunk(unsigned char *ring, int slot, int tid,
                                             const T *qr, const T *qdr, const T *qddr, int i0)
@@ -280,8 +289,8 @@ __device__ __forceinline__ void stage_chunk(unsigned char *ring, int slot, int t
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int h = 0; h < P; ++h)
-            __pipeline_memcpy_async(&r[((slot * 3 + a) * P + h) * BLOCK + tid],
-                                    src[a] + i0 + h * (16 / (int)sizeof(T)), 16);
+            cp_async16_cg(&r[((slot * 3 + a) * P + h) * BLOCK + tid],
+                          src[a] + i0 + h * (16 / (int)sizeof(T)));
 }
 
 template <typename T, int BLOCK>
