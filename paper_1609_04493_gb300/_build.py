@@ -65,7 +65,7 @@ def build(force=False, verbose=False, extra_flags=()):
             print(r.stdout, r.stderr, flush=True)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 8, 8), len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = SO + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared",
