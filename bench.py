@@ -364,12 +364,14 @@ class Peaks:
 
 def adjoint_section(torch, rd, chaingen, model, dev, dist, sampler, K):
     """Seconds per rnea_vjp call at n = 32 FP32: recompute (the library's
-    mapping) at B = 4096, 8192 and 262144, store at 8192, and at 8192 each
+    mapping) at B = 4096, 8192 and 262144, store at 8192 and 262144 (the
+    workspace then holds 671 MB of forward state), and at 8192 each
     mapping by flag: one thread, shared-memory state, 8 lanes, two warps, two
     warps with shared-memory state."""
     raw = {}
     R = rd.RD_VJP_RECOMPUTE
-    for B, mode in ((4096, R), (8192, R), (262144, R), (8192, rd.RD_VJP_STORE)):
+    for B, mode in ((4096, R), (8192, R), (262144, R), (8192, rd.RD_VJP_STORE),
+                    (262144, rd.RD_VJP_STORE)):
         sets = []
         nsets = 2 if B > 100000 else 8
         for r in range(nsets):
