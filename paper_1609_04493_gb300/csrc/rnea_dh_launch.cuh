@@ -208,10 +208,18 @@ void dhp_default_kr(const rd_model *m, int B, int &K, int &RL, int &stages)
         RL = n;
         return;
     }
-    int per_sm = 0;
-    const size_t smem = dhp_smem_per_thread<float>(n, n, 4, 2) * 32;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rnea_dhp_kernel<float, 32, 32, TRIG, 4, 2>,
-                                                  32, smem);
+    // resident blocks per SM of the RL = 4, two-chunk kernel at this n, queried
+    // once per device, length and sin/cos variant (stored + 1; 0 = not yet known)
+    static std::atomic<int> known[64][33][2];
+    std::atomic<int> &slot = known[m->device & 63][n][TRIG == kTrigSfu ? 1 : 0];
+    int per_sm = slot.load() - 1;
+    if (per_sm < 0) {
+        per_sm = 0;
+        const size_t smem = dhp_smem_per_thread<float>(n, n, 4, 2) * 32;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, rnea_dhp_kernel<float, 32, 32, TRIG, 4, 2>, 32, smem);
+        slot.store(per_sm + 1);
+    }
     const long long sms = dh_device_attr(m->device, cudaDevAttrMultiProcessorCount, 1);
     if ((long long)per_sm * sms >= 2 * ((long long)(B + 31) / 32)) {
         RL = 4;
