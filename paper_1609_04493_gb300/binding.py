@@ -624,16 +624,14 @@ def jsiia(model, q, qd, tau, base=None, status=None, out=None, stream=None):
 def forward_dynamics(model, q, qd, tau, method="auto", base=None, status=None, workspace=None,
                      out=None, stream=None):
     """qdd = FD(q, qd, tau) by the articulated-body algorithm (aba_batch) or the
-    joint-space-inertia solve (jsiia_batch). ``auto`` follows the crossover
-    measured on GB300: JSIIA for FP32 chains of at most 32 links in batches of
-    at most 512 (each instance spread over a warp; e.g. n = 32, B = 256: 111 us
-    vs 142 us), the articulated-body algorithm otherwise (e.g. n = 32,
-    B = 1024: 140 us vs 165 us; B = 8192: 159 us vs 1034 us; FP64: always)."""
-    import torch
-
+    joint-space-inertia solve (jsiia_batch). ``auto`` takes the articulated-body
+    algorithm, which on GB300 leads at every size measured once small batches
+    run with three warps per 32 instances (FP32, µs, JSIIA / ABA: n = 8, B = 256:
+    30.3 / 19.8; n = 16: 62.2 / 39.0; n = 32, B = 32 / 256 / 1024: 108 / 78.5,
+    108.5 / 78.8, 162 / 79.8; larger batches and FP64: ABA by a wider margin).
+    ``jsiia`` stays available (n <= 32)."""
     if method == "auto":
-        small = q.shape[0] <= 512 and model.n <= 32 and q.dtype == torch.float32
-        method = "jsiia" if small else "aba"
+        method = "aba"
     if method == "jsiia":
         return jsiia(model, q, qd, tau, base=base, status=status, out=out, stream=stream)
     if method == "aba":

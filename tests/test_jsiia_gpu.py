@@ -75,6 +75,8 @@ def test_forward_dynamics_auto_dispatch(cuda_lib):
         ch = chaingen.make_chain(n, seed=11)
         st = chaingen.make_states(B, n, seed=12, kinds=("q", "qd", "tau"))
         x = [torch.from_numpy(st[k].astype(np.float32)).cuda() for k in ("q", "qd", "tau")]
-        qdd = cuda_lib.forward_dynamics(cuda_lib.Model(ch), *x).cpu().double().numpy()
+        model = cuda_lib.Model(ch)
+        auto = cuda_lib.forward_dynamics(model, *x)
+        assert torch.equal(auto, cuda_lib.aba(model, *x))  # auto takes the ABA
         ref = oracle.fd_aba(ch, *(a.cpu().double().numpy() for a in x))
-        assert oracle.rel_err(qdd, ref) <= TOL["float32"]
+        assert oracle.rel_err(auto.cpu().double().numpy(), ref) <= TOL["float32"]
