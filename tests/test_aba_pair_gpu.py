@@ -212,3 +212,13 @@ def test_bench_fd_configuration_sampled(cuda_lib, n, prec):
     idx = np.arange(0, 16384, 64)
     ref = oracle.fd_aba(ch, h["q"][idx], h["qd"][idx], h["tau"][idx])
     assert oracle.rel_err(qdd[idx], ref) <= TOL["float32"]
+
+
+def test_empty_batch(cuda_lib, mapping):
+    """B = 0 with the mapping flag set: nothing launches, the call succeeds."""
+    import torch
+
+    model = cuda_lib.Model(chaingen.make_chain(12))
+    x = torch.zeros((0, 12), device="cuda")
+    qdd = cuda_lib.aba(model, x, x, x, flags=mapping)
+    assert qdd.shape == (0, 12)

@@ -384,3 +384,12 @@ def test_register_state_rejections(cuda_lib):
     with pytest.raises(cuda_lib.RdError):  # FP64
         cuda_lib.rnea(m16, x16d, x16d, x16d, variant=base_v | cuda_lib.RD_TUNE_STORED_LINKS(16) |
                       cuda_lib.RD_TUNE_REG_STATE_LINKS(8))
+
+
+def test_register_state_empty_batch(cuda_lib):
+    torch = _torch()
+    model = cuda_lib.Model(chaingen.make_chain(32))
+    z = torch.zeros((0, 32), device="cuda")
+    v = (cuda_lib.RD_VARIANT_SERIAL_DH | cuda_lib.RD_TUNE_BLOCK(32) | cuda_lib.RD_TUNE_STORED_LINKS(32)
+         | cuda_lib.RD_TUNE_REG_STATE_LINKS(8) | cuda_lib.RD_TUNE_TWO_STAGE_RING)
+    assert cuda_lib.rnea(model, z, z, z, variant=v).shape == (0, 32)

@@ -472,3 +472,12 @@ def test_vjp_auto_picks_the_measured_mapping(cuda_lib, n, B, flag):
     b = cuda_lib.rnea_vjp(model, *x, mode=rec | pick)
     for u, v in zip(a, b):
         assert torch.equal(u, v)
+
+
+def test_vjp_duo_empty_batch(cuda_lib):
+    import torch
+
+    model = cuda_lib.Model(chaingen.make_chain(16))
+    x = torch.zeros((0, 16), device="cuda")
+    g = cuda_lib.rnea_vjp(model, x, x, x, x, mode=_duo(cuda_lib))
+    assert all(t.shape == (0, 16) for t in g)
