@@ -150,7 +150,8 @@ def parse_args():
     p.add_argument("--kernel-only",
                    choices=["f32", "f64", "f64df", "host", "vjp", "vjplane", "vjppair", "vjpsmem",
                             "aba", "aba64",
-                            "abawarp", "abapair", "abatri", "fleet", "fleetpair", "fleettri64"],
+                            "abawarp", "abapair", "abatri", "abatri1k", "fleet", "fleetpair",
+                            "fleettri64"],
                    default=None,
                    help="profiling case: W + K plain launches of one kernel, no JSON "
                         "(f32/f64: RNEA n=32 B=65536; f64df: the same FP64 data in double-float "
@@ -160,7 +161,8 @@ def parse_args():
                         "instances / state in shared memory; aba: forward dynamics n=64 B=16384 (double-float updates; "
                         "aba64: FP64 updates); abawarp: forward dynamics n=64 B=1024, one warp per "
                         "instance; abapair / abatri: forward dynamics n=64 B=16384, two / three "
-                        "warps per 32 instances; fleet: 20000 mixed requests; fleetpair: the same "
+                        "warps per 32 instances; abatri1k: three warps at B=1024; fleet: 20000 "
+                        "mixed requests; fleetpair: the same "
                         "with warp pairs for forward-dynamics chains from 65 links; fleettri64: "
                         "warp triples from 65 links, FP64 updates)")
     return p.parse_args()
@@ -861,13 +863,14 @@ def run_kernel_only(args):
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "qdd", "w")]
         for _ in range(calls):
             res = rd.rnea_vjp(model, *x, mode=mode)[0]
-    elif args.kernel_only in ("aba", "aba64", "abawarp", "abapair", "abatri"):
+    elif args.kernel_only in ("aba", "aba64", "abawarp", "abapair", "abatri", "abatri1k"):
         flags = {"aba": rd.RD_ABA_THREAD_PER_INSTANCE,
                  "aba64": rd.RD_ABA_FP64_UPDATE | rd.RD_ABA_THREAD_PER_INSTANCE,
                  "abawarp": rd.RD_ABA_WARP_PER_INSTANCE,
                  "abapair": rd.RD_ABA_TWO_WARPS,
-                 "abatri": rd.RD_ABA_THREE_WARPS}[args.kernel_only]
-        Ba = 1024 if args.kernel_only == "abawarp" else 16384
+                 "abatri": rd.RD_ABA_THREE_WARPS,
+                 "abatri1k": rd.RD_ABA_THREE_WARPS}[args.kernel_only]
+        Ba = 1024 if args.kernel_only in ("abawarp", "abatri1k") else 16384
         model = rd.Model(chaingen.make_chain(64, seed=chaingen.BASE_SEED))
         st = chaingen.make_states(Ba, 64, seed=6000, kinds=("q", "qd", "tau"))
         x = [torch.from_numpy(st[k]).to(dev, torch.float32) for k in ("q", "qd", "tau")]
